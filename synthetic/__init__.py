@@ -1,0 +1,263 @@
+"""Seeded synthetic inputs for the Gaussian-splatting hot path.
+
+The paper's data (FAST-LIVO and R3LIVE sequences, 640x512 images) are not
+available, so every workload is synthetic.  This module only draws inputs:
+Gaussian parameters (from a simulated LiDAR sweep for the large workloads),
+camera poses, target images and sparse LiDAR depth targets.  It holds none
+of the rendering, loss or gradient arithmetic, and both the CUDA tests and
+the oracle tests draw their inputs from it.
+
+All arrays are float32 numpy arrays in the layouts the library takes:
+means [N,3], log_scales [N,3], quats [N,4] (w,x,y,z, not normalised),
+opacity_logits [N], sh [N,K,3] with K = (max degree + 1)^2.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+BASE_SEED = 20241105
+
+
+@dataclass
+class CameraSpec:
+    """World->camera rotation R (row-major 3x3), translation t, level-0 pinhole."""
+    R: np.ndarray
+    t: np.ndarray
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    W: int
+    H: int
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def random_quats(rng, n):
+    q = rng.standard_normal((n, 4)).astype(np.float32)
+    q /= np.linalg.norm(q, axis=1, keepdims=True).astype(np.float32)
+    return q.astype(np.float32)
+
+
+def identity_camera(W, H, f, cx=None, cy=None):
+    return CameraSpec(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), float(f), float(f),
+                      float(W / 2 if cx is None else cx), float(H / 2 if cy is None else cy), W, H)
+
+
+def small_scene(seed=BASE_SEED + 1, n=2000, W=160, H=120, f=150.0, xy=4.0, z=(2.0, 10.0),
+                sh_degree=0, sh_max_degree=None, log_scale=(-3.0, 0.5), lidar_frac=0.05):
+    """The 160x120 single-view workload: uniform means in front of an identity camera.
+
+    Means x,y ~ U[-xy, xy], z ~ U[z]; log-scales ~ N(log_scale); random unit
+    quaternions; opacity logits ~ N(0,1); SH band 0 chosen so the base colour
+    is U[0,1] (coefficient U[-sqrt(pi), sqrt(pi)]), higher bands ~ N(0, 0.1).
+    Target RGB ~ U[0,1] per pixel; LiDAR depth U[z] at ``lidar_frac`` of the
+    pixels (chosen without replacement), 0 elsewhere.
+    """
+    rng = _rng(seed)
+    kmax = sh_degree if sh_max_degree is None else sh_max_degree
+    K = (kmax + 1) ** 2
+    means = np.empty((n, 3), np.float32)
+    means[:, 0] = rng.uniform(-xy, xy, n)
+    means[:, 1] = rng.uniform(-xy, xy, n)
+    means[:, 2] = rng.uniform(z[0], z[1], n)
+    log_scales = rng.normal(log_scale[0], log_scale[1], (n, 3)).astype(np.float32)
+    quats = random_quats(rng, n)
+    opacity_logits = rng.normal(0.0, 1.0, n).astype(np.float32)
+    sh = np.zeros((n, K, 3), np.float32)
+    sh[:, 0, :] = rng.uniform(-math.sqrt(math.pi), math.sqrt(math.pi), (n, 3))
+    if K > 1:
+        sh[:, 1:, :] = rng.normal(0.0, 0.1, (n, K - 1, 3))
+    params = dict(means=means, log_scales=log_scales, quats=quats,
+                  opacity_logits=opacity_logits, sh=sh, sh_degree=sh_degree)
+    cam = identity_camera(W, H, f)
+    gt = rng.uniform(0.0, 1.0, (3, H, W)).astype(np.float32)
+    lidar = np.zeros(H * W, np.float32)
+    k = int(round(lidar_frac * H * W))
+    idx = rng.choice(H * W, size=k, replace=False)
+    lidar[idx] = rng.uniform(z[0], z[1], k)
+    return params, cam, gt, lidar.reshape(H, W)
+
+
+# ---------------------------------------------------------------------------
+# LiDAR-sweep scenes for the 1280x1024 workloads
+# ---------------------------------------------------------------------------
+
+def _boxes(rng, n_boxes=40):
+    """Axis-aligned facades beside a trajectory along +x (footprint 5-20 m, height 3-15 m)."""
+    lo = np.zeros((n_boxes, 3))
+    hi = np.zeros((n_boxes, 3))
+    for i in range(n_boxes):
+        sx, sy = rng.uniform(5, 20, 2)
+        h = rng.uniform(3, 15)
+        cxw = rng.uniform(-20, 80)
+        side = rng.choice([-1.0, 1.0])
+        dist = rng.uniform(8, 50)
+        cyw = side * (dist + sy / 2)
+        lo[i] = (cxw - sx / 2, cyw - sy / 2, 0.0)
+        hi[i] = (cxw + sx / 2, cyw + sy / 2, h)
+    return lo, hi
+
+
+def _texture(p):
+    """Procedural colour of a world position (structured, in [0,1])."""
+    r = 0.5 + 0.35 * np.sin(0.9 * p[:, 0] + 0.3 * p[:, 2]) * np.cos(0.7 * p[:, 1])
+    g = 0.5 + 0.35 * np.sin(0.5 * p[:, 1] + 1.3 * p[:, 2] + 1.0)
+    b = 0.5 + 0.35 * np.cos(0.6 * p[:, 0] - 0.8 * p[:, 1] + 0.5 * p[:, 2])
+    stripes = 0.12 * np.sign(np.sin(3.0 * p[:, 0]) * np.sin(3.0 * p[:, 1] + 2.0 * p[:, 2]))
+    return np.clip(np.stack([r, g, b], 1) + stripes[:, None], 0.0, 1.0)
+
+
+def lidar_sweep(origin, lo, hi, n_beams=64, az_step_deg=0.2, elev=(-25.0, 15.0), rng_lim=(2.0, 60.0)):
+    """Ray-cast one 360-degree sweep against the ground plane z=0 and the boxes."""
+    el = np.deg2rad(np.linspace(elev[0], elev[1], n_beams))
+    az = np.deg2rad(np.arange(0.0, 360.0, az_step_deg))
+    E, A = np.meshgrid(el, az, indexing="ij")
+    d = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    tbest = np.full(d.shape[0], np.inf)
+    down = d[:, 2] < 0
+    tbest[down] = origin[2] / (-d[down, 2])
+    inv = 1.0 / np.where(np.abs(d) < 1e-12, 1e-12, d)
+    for c0 in range(0, d.shape[0], 16384):
+        sl = slice(c0, c0 + 16384)
+        t0 = (lo[None] - origin) * inv[sl, None, :]
+        t1 = (hi[None] - origin) * inv[sl, None, :]
+        tmin = np.minimum(t0, t1).max(2)
+        tmax = np.maximum(t0, t1).min(2)
+        tmin = np.where((tmax >= tmin) & (tmin > 0), tmin, np.inf).min(1)
+        tbest[sl] = np.minimum(tbest[sl], tmin)
+    keep = (tbest >= rng_lim[0]) & (tbest <= rng_lim[1])
+    return origin + d[keep] * tbest[keep, None]
+
+
+def trajectory_pose(s, seed_phase=0.0, length=50.0, height=1.8):
+    """Camera/sensor pose at arc position s in [0,1] of a 50 m straight path with a yaw sinusoid."""
+    x = s * length
+    yaw = 0.25 * math.sin(2 * math.pi * s * 1.5 + seed_phase)
+    y = 0.8 * math.sin(2 * math.pi * s + seed_phase)
+    return np.array([x, y, height]), yaw
+
+
+def camera_at(pos, yaw, W=1280, H=1024, f=860.0):
+    """World->camera pose of a forward-looking camera (x right, y down, z forward)."""
+    fwd = np.array([math.cos(yaw), math.sin(yaw), 0.0])
+    right = np.array([math.sin(yaw), -math.cos(yaw), 0.0])
+    down = np.array([0.0, 0.0, -1.0])
+    R = np.stack([right, down, fwd]).astype(np.float32)
+    t = (-R.astype(np.float64) @ pos).astype(np.float32)
+    return CameraSpec(R, t, float(f), float(f), W / 2.0, H / 2.0, W, H)
+
+
+def lidar_scene(n, seed=BASE_SEED + 2, sh_degree=3, log_scale=(-3.0, 0.5)):
+    """Gaussians initialised from a seeded LiDAR map: sweeps along the trajectory until n points.
+
+    64 beams over [-25, 15] degrees, 0.2 degree azimuth, hits in [2, 60] m on a
+    ground plane plus 40 box facades; colour from a procedural texture; SH
+    band 0 set from the colour, higher bands ~ N(0, 0.1); opacity logit
+    ~ N(0,1); log-scale ~ N(log_scale); random unit quaternions.
+    """
+    rng = _rng(seed)
+    lo, hi = _boxes(rng)
+    phase = float(rng.uniform(0, 2 * math.pi))
+    pts = []
+    total = 0
+    k = 0
+    n_pos = 16
+    while True:
+        # sweeps at evenly spaced positions, then at the midpoints between them, ...
+        rnd, j = divmod(k, n_pos)
+        s = (j + 0.5 + (0.5 * rnd) % 1.0) / n_pos
+        origin, _ = trajectory_pose(s, phase)
+        p = lidar_sweep(origin, lo, hi)
+        pts.append(p)
+        total += p.shape[0]
+        k += 1
+        if k % n_pos == 0 and total >= n:
+            break
+    P = np.concatenate(pts)
+    P = P[rng.choice(P.shape[0], size=n, replace=False)]
+    col = _texture(P)
+    K = (sh_degree + 1) ** 2
+    sh = np.zeros((n, K, 3), np.float32)
+    sh[:, 0, :] = (col - 0.5) * (2.0 * math.sqrt(math.pi))
+    if K > 1:
+        sh[:, 1:, :] = rng.normal(0.0, 0.1, (n, K - 1, 3))
+    params = dict(means=P.astype(np.float32),
+                  log_scales=rng.normal(log_scale[0], log_scale[1], (n, 3)).astype(np.float32),
+                  quats=random_quats(rng, n),
+                  opacity_logits=rng.normal(0.0, 1.0, n).astype(np.float32),
+                  sh=sh, sh_degree=sh_degree)
+    return params, phase
+
+
+def trajectory_cameras(n_views, seed=BASE_SEED + 3, phase=0.0, W=1280, H=1024, f=860.0):
+    """Keyframe cameras at seeded positions along the trajectory."""
+    rng = _rng(seed)
+    ss = np.sort(rng.uniform(0.05, 0.95, n_views))
+    cams = []
+    for s in ss:
+        pos, yaw = trajectory_pose(float(s), phase)
+        cams.append(camera_at(pos, yaw, W, H, f))
+    return cams
+
+
+def target_images(cam: CameraSpec, seed, lidar_frac=0.05, depth_range=(2.0, 60.0)):
+    """Level-0 targets for one keyframe: a structured colour image and sparse LiDAR depth.
+
+    The image is a smooth colour field with sharp bands and noise; the depth
+    target is nonzero on ``lidar_frac`` of the pixels, grouped in 64 scan
+    rows, with a smooth depth field in ``depth_range``.
+    """
+    rng = _rng(seed)
+    H, W = cam.H, cam.W
+    yy, xx = np.meshgrid(np.linspace(0, 1, H), np.linspace(0, 1, W), indexing="ij")
+    ph = rng.uniform(0, 2 * math.pi, 6)
+    img = np.stack([
+        0.5 + 0.3 * np.sin(7 * xx + ph[0]) * np.cos(5 * yy + ph[1]),
+        0.5 + 0.3 * np.sin(11 * xx * yy + ph[2]),
+        0.5 + 0.3 * np.cos(9 * yy + ph[3]) * np.sin(3 * xx + ph[4]),
+    ])
+    img += 0.15 * (np.sin(40 * xx + 13 * yy + ph[5]) > 0.6)
+    img += rng.normal(0, 0.03, img.shape)
+    img = np.clip(img, 0, 1).astype(np.float32)
+    depth = np.zeros((H, W), np.float32)
+    rows = np.linspace(H * 0.35, H - 1, 64).astype(int)
+    k = int(lidar_frac * H * W)
+    per_row = max(1, k // rows.shape[0])
+    field = depth_range[0] + (depth_range[1] - depth_range[0]) * (
+        0.5 + 0.5 * np.sin(3 * xx + ph[0]) * np.cos(2 * yy + ph[1]))
+    for r in rows:
+        cols = rng.choice(W, size=min(W, per_row), replace=False)
+        depth[r, cols] = field[r, cols]
+    return img, depth
+
+
+def mixed_level_views(n_views, seed=BASE_SEED + 4, levels=(0, 1, 2)):
+    """Pyramid level per keyframe, drawn uniformly from ``levels``."""
+    rng = _rng(seed)
+    return [int(v) for v in rng.choice(levels, size=n_views)]
+
+
+def workload(name):
+    """Named workloads (all seeded).  Returns a dict of params, cameras, levels, targets."""
+    if name == "small_160x120_2k":
+        params, cam, gt, lidar = small_scene()
+        return dict(params=params, cams=[cam], levels=[0], gts=[gt], lidars=[lidar],
+                    lam=0.0, lam_d=1.0)
+    if name.startswith("lidar_"):
+        # lidar_<N>_<V>v : N Gaussians, V keyframes at mixed levels
+        _, n, v = name.split("_")
+        n = int(n)
+        V = int(v.rstrip("v"))
+        params, phase = lidar_scene(n)
+        cams = trajectory_cameras(V, phase=phase)
+        levels = [0] if V == 1 else mixed_level_views(V)
+        tg = [target_images(c, BASE_SEED + 100 + i) for i, c in enumerate(cams)]
+        return dict(params=params, cams=cams, levels=levels, gts=[t[0] for t in tg],
+                    lidars=[t[1] for t in tg], lam=0.2, lam_d=0.1)
+    raise KeyError(name)

@@ -1,0 +1,487 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+(one or two isotropic Gaussians, constant images), invariants (weights plus
+final transmittance sum to one), library routines (numpy sort / eigvalsh /
+scipy's complex spherical harmonics and correlate), finite differences of the
+projection and of the whole loss, and brute-force enumeration.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synthetic as S
+
+
+def cam_of(spec):
+    return O.Camera(spec.R, spec.t, spec.fx, spec.fy, spec.cx, spec.cy, spec.W, spec.H)
+
+
+def one_gaussian_params(means, log_s, logits, colours, quats=None):
+    n = len(means)
+    sh = np.zeros((n, 1, 3), np.float32)
+    sh[:, 0, :] = (np.asarray(colours) - 0.5) * math.sqrt(4 * math.pi)  # Y_00 = 1/sqrt(4 pi)
+    q = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)) if quats is None else quats
+    return dict(means=np.asarray(means, np.float32),
+                log_scales=np.full((n, 3), 0, np.float32) + np.asarray(log_s, np.float32)[:, None],
+                quats=np.asarray(q, np.float32), opacity_logits=np.asarray(logits, np.float32),
+                sh=sh, sh_degree=0)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+# --------------------------------------------------------------------------
+# a5 closed forms (Eq. 3-6): one and two isotropic Gaussians on the optical axis
+# --------------------------------------------------------------------------
+def test_single_isotropic_gaussian_closed_form():
+    W, H, f = 64, 48, 50.0
+    cam = O.Camera(np.eye(3), np.zeros(3), f, f, 32.0, 24.0, W, H)
+    z, s, logit, col = 4.0, 0.2, 1.0, np.array([0.9, 0.5, 0.2])
+    p = one_gaussian_params([[0, 0, z]], [math.log(s)], [logit], [col])
+    r = O.render_view(p, cam, 0)
+    s_eff = math.exp(float(np.float32(math.log(s))))  # the parameter is a binary32 log-scale
+    sig2 = (f * s_eff / z) ** 2 + 0.3
+    # radius from the eigenvalues of sig2*I (both equal; discriminant floored at 0.1)
+    rad = math.ceil(3 * math.sqrt(sig2 + math.sqrt(0.1)))
+    assert r["pre"]["radius"][0] == rad
+    o = sigmoid(logit)
+    yy, xx = np.mgrid[0:H, 0:W]
+    a = o * np.exp(-((xx - 32.0) ** 2 + (yy - 24.0) ** 2) / (2 * sig2))
+    a = np.minimum(a, 0.99)
+    a[a < 1 / 255] = 0
+    # only the tiles of the covered rectangle are composited
+    x0, x1 = int((32 - rad) / 16), int((32 + rad + 15) / 16)
+    y0, y1 = int((24 - rad) / 16), int((24 + rad + 15) / 16)
+    cover = np.zeros((H, W), bool)
+    cover[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
+    a[~cover] = 0
+    np.testing.assert_allclose(r["alpha"], a, atol=1e-12)
+    np.testing.assert_allclose(r["depth"], z * a, atol=1e-11)
+    for ch in range(3):
+        np.testing.assert_allclose(r["rgb"][ch], col[ch] * a, atol=1e-12)
+    np.testing.assert_allclose(r["final_T"], 1 - a, atol=1e-12)
+
+
+def test_two_gaussians_closed_form():
+    W, H, f = 32, 32, 40.0
+    cam = O.Camera(np.eye(3), np.zeros(3), f, f, 16.0, 16.0, W, H)
+    c1, c2 = np.array([1.0, 0.2, 0.1]), np.array([0.1, 0.8, 0.6])
+    # the nearer Gaussian is listed second to check the depth ordering
+    # both on the optical axis, where the projected covariance is isotropic
+    p = one_gaussian_params([[0, 0, 6.0], [0, 0, 3.0]], [math.log(0.3), math.log(0.15)],
+                            [0.5, -0.2], [c2, c1])
+    r = O.render_view(p, cam, 0, tile=(32, 32))
+    o1, o2 = sigmoid(-0.2), sigmoid(0.5)
+    s1 = (f * math.exp(float(np.float32(math.log(0.15)))) / 3.0) ** 2 + 0.3
+    s2 = (f * math.exp(float(np.float32(math.log(0.3)))) / 6.0) ** 2 + 0.3
+    u2 = 16.0
+    for (px, py) in [(16, 16), (18, 15), (20, 20), (13, 17)]:
+        a1 = min(0.99, o1 * math.exp(-((px - 16) ** 2 + (py - 16) ** 2) / (2 * s1)))
+        a2 = min(0.99, o2 * math.exp(-((px - u2) ** 2 + (py - 16) ** 2) / (2 * s2)))
+        a1 = a1 if a1 >= 1 / 255 else 0.0
+        a2 = a2 if a2 >= 1 / 255 else 0.0
+        C = c1 * a1 + c2 * a2 * (1 - a1)
+        D = 3.0 * a1 + 6.0 * a2 * (1 - a1)
+        np.testing.assert_allclose(r["rgb"][:, py, px], C, atol=1e-6)
+        np.testing.assert_allclose(r["depth"][py, px], D, atol=1e-5)
+        np.testing.assert_allclose(r["alpha"][py, px], 1 - (1 - a1) * (1 - a2), atol=1e-6)
+
+
+# --------------------------------------------------------------------------
+# a5 invariants: sum_i alpha_i T_i + T_final = 1, T bounded by the stop rule
+# --------------------------------------------------------------------------
+def test_weights_plus_transmittance_is_one():
+    params, spec, _, _ = S.small_scene()
+    params = dict(params)
+    sh = params["sh"].copy()
+    sh[:, 0, :] = 0.5 * math.sqrt(4 * math.pi)  # every colour = 1
+    params["sh"] = sh
+    r = O.render_view(params, cam_of(spec), 0)
+    for ch in range(3):
+        np.testing.assert_allclose(r["rgb"][ch] + r["final_T"], 1.0, atol=1e-12)
+    assert (r["final_T"] >= 1e-4).all() and (r["final_T"] <= 1).all()
+    assert (r["alpha"] >= 0).all() and (r["alpha"] <= 1).all()
+    assert r["n_contrib"].max() > 5
+
+
+def test_early_stop_closed_form():
+    # 20 identical on-axis Gaussians with opacity 1/2: alpha = 1/2 exactly at the centre pixel,
+    # T after k of them is 2^-k; 2^-13 >= 1e-4 > 2^-14, so the 14th is excluded and the pixel stops.
+    W = H = 16
+    cam = O.Camera(np.eye(3), np.zeros(3), 20.0, 20.0, 8.0, 8.0, W, H)
+    n = 20
+    cols = np.random.default_rng(9).uniform(0.1, 0.9, (n, 3))
+    p = one_gaussian_params([[0, 0, 2.0 + 0.25 * i] for i in range(n)], [math.log(0.05)] * n,
+                            [0.0] * n, cols)
+    r = O.render_view(p, cam, 0)
+    w = 0.5 * 0.5 ** np.arange(13)
+    assert r["n_contrib"][8, 8] == 13
+    assert r["final_T"][8, 8] == pytest.approx(2.0 ** -13, rel=1e-14)
+    # colours pass through a binary32 SH coefficient, hence the looser tolerance
+    np.testing.assert_allclose(r["rgb"][:, 8, 8], (cols[:13] * w[:, None]).sum(0), rtol=1e-6)
+    np.testing.assert_allclose(r["depth"][8, 8], ((2.0 + 0.25 * np.arange(13)) * w).sum(), rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# a1: EWA covariance against a finite-difference Jacobian of the projection
+# --------------------------------------------------------------------------
+def _quat_R(q):
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_projection_covariance_matches_fd_jacobian():
+    rng = np.random.default_rng(5)
+    n = 40
+    ang = rng.normal(size=3)
+    Rw = _quat_R(np.array([1.0, *(0.1 * ang)]))
+    t = np.array([0.2, -0.1, 0.5])
+    cam = O.Camera(Rw.astype(np.float32), t.astype(np.float32), 300.0, 280.0, 160.0, 120.0, 320, 240)
+    means = np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(3, 8, n)], 1)
+    params = dict(means=means.astype(np.float32),
+                  log_scales=rng.normal(-2.5, 0.4, (n, 3)).astype(np.float32),
+                  quats=rng.normal(size=(n, 4)).astype(np.float32),
+                  opacity_logits=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32),
+                  sh_degree=0)
+    pre = O.preprocess(params, cam)
+    Rd, td = np.asarray(cam.R, np.float64), np.asarray(cam.t, np.float64)
+
+    def proj(p):
+        return np.array([cam.fx * p[0] / p[2] + cam.cx, cam.fy * p[1] / p[2] + cam.cy])
+
+    for i in range(n):
+        pc = Rd @ means[i].astype(np.float32).astype(np.float64) + td
+        Jfd = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = 1e-6
+            Jfd[:, k] = (proj(pc + e) - proj(pc - e)) / 2e-6
+        Rq = _quat_R(params["quats"][i].astype(np.float64))
+        s = np.exp(params["log_scales"][i].astype(np.float64))
+        Sig = Rq @ np.diag(s * s) @ Rq.T
+        cov = Jfd @ Rd @ Sig @ Rd.T @ Jfd.T + 0.3 * np.eye(2)
+        inv = np.linalg.inv(cov)
+        np.testing.assert_allclose(pre["conic"][i], [inv[0, 0], inv[0, 1], inv[1, 1]],
+                                   rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(pre["uv"][i], proj(pc), rtol=1e-12)
+        assert pre["depth"][i] == pytest.approx(pc[2], rel=1e-12)
+
+
+def test_quaternion_sign_invariance_and_radius_eigen():
+    params, spec, _, _ = S.small_scene(n=500)
+    cam = cam_of(spec)
+    pre = O.preprocess(params, cam)
+    neg = dict(params); neg["quats"] = -params["quats"]
+    pre2 = O.preprocess(neg, cam)
+    np.testing.assert_array_equal(pre["rect"], pre2["rect"])
+    np.testing.assert_array_equal(pre["radius"], pre2["radius"])
+    np.testing.assert_allclose(pre["conic"], pre2["conic"], rtol=1e-12)
+    vis = pre["tiles"] > 0
+    checked = 0
+    for i in np.nonzero(vis)[0]:
+        A, B, C = pre["conic"][i]
+        cov = np.linalg.inv(np.array([[A, B], [B, C]]))
+        lam = np.linalg.eigvalsh(cov)
+        mid = 0.5 * (lam[0] + lam[1])
+        r_expect = 3 * math.sqrt(mid + math.sqrt(max(0.1, (0.5 * (lam[1] - lam[0])) ** 2)))
+        if abs(r_expect - round(r_expect)) < 1e-3:
+            continue  # too close to an integer for a binary32 / binary64 comparison
+        assert pre["radius"][i] == math.ceil(r_expect)
+        checked += 1
+    assert checked > 100
+
+
+def test_tile_rect_covers_three_sigma_ellipse():
+    params, spec, _, _ = S.small_scene(n=400)
+    cam = cam_of(spec)
+    pre = O.preprocess(params, cam)
+    T = 16
+    for i in np.nonzero(pre["tiles"] > 0)[0]:
+        A, B, C = pre["conic"][i]
+        cov = np.linalg.inv(np.array([[A, B], [B, C]]))
+        hx, hy = 3 * math.sqrt(cov[0, 0]), 3 * math.sqrt(cov[1, 1])  # ellipse bounding box
+        u, v = pre["uv"][i]
+        x0, y0, x1, y1 = pre["rect"][i]
+        lo_x, hi_x = max(0.0, u - hx), min(cam.W - 1.0, u + hx)
+        lo_y, hi_y = max(0.0, v - hy), min(cam.H - 1.0, v + hy)
+        # the rectangle (x0 = trunc((u-r)/T), x1 = trunc((u+r+T-1)/T)) covers every pixel
+        # column in [u - r, u + r - 1], and r >= 3 sigma along each axis
+        if lo_x <= hi_x - 1 and lo_y <= hi_y - 1:
+            assert x0 * T <= math.ceil(lo_x) and math.floor(hi_x - 1) <= x1 * T - 1
+            assert y0 * T <= math.ceil(lo_y) and math.floor(hi_y - 1) <= y1 * T - 1
+
+
+# --------------------------------------------------------------------------
+# a2-a4: keys, sort order and ranges by brute-force enumeration + numpy sort
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 16)])
+def test_keys_sort_ranges_brute_force(tile):
+    params, spec, _, _ = S.small_scene()
+    cam = cam_of(spec)
+    pre = O.preprocess(params, cam, tile)
+    tx_n = pre["tiles_x"]
+    keys, vals = [], []
+    for i in range(pre["tiles"].shape[0]):
+        x0, y0, x1, y1 = pre["rect"][i]
+        if pre["tiles"][i] == 0:
+            continue
+        zb = int(pre["z_f"][i:i + 1].view(np.uint32)[0])
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append(((ty * tx_n + tx) << 32) | zb)
+                vals.append(i)
+    keys = np.array(keys, np.uint64)
+    vals = np.array(vals, np.uint32)
+    order = np.lexsort((vals, keys))
+    ok, ov = O.build_keys(pre)
+    np.testing.assert_array_equal(ok, keys[order])
+    np.testing.assert_array_equal(ov, vals[order])
+    n_tiles = tx_n * pre["tiles_y"]
+    rg = O.tile_ranges(ok, n_tiles)
+    tid = (ok >> np.uint64(32)).astype(np.int64)
+    for t in range(n_tiles):
+        idx = np.nonzero(tid == t)[0]
+        if idx.size == 0:
+            assert rg[t, 0] == rg[t, 1] == 0
+        else:
+            assert rg[t, 0] == idx[0] and rg[t, 1] == idx[-1] + 1
+            assert (np.diff(idx) == 1).all()
+
+
+def test_depth_key_is_float_order():
+    # positive binary32 values order like their bit patterns (what the key relies on)
+    z = np.sort(np.random.default_rng(0).uniform(0.2, 1000, 10000).astype(np.float32))
+    assert (np.diff(z.view(np.uint32).astype(np.int64)) >= 0).all()
+
+
+# --------------------------------------------------------------------------
+# SH basis: orthonormal (quadrature), equal to scipy's complex SH made real
+# --------------------------------------------------------------------------
+def _sphere_quadrature(n_t=40, n_p=80):
+    xg, wg = np.polynomial.legendre.leggauss(n_t)
+    phi = (np.arange(n_p) + 0.5) * 2 * math.pi / n_p
+    pts, wts = [], []
+    for ct, w in zip(xg, wg):
+        st = math.sqrt(1 - ct * ct)
+        for p in phi:
+            pts.append((st * math.cos(p), st * math.sin(p), ct))
+            wts.append(w * 2 * math.pi / n_p)
+    return np.array(pts), np.array(wts)
+
+
+def test_sh_orthonormal():
+    pts, wts = _sphere_quadrature()
+    Y = np.array([O.sh_basis(p)[0] for p in pts])
+    G = (Y * wts[:, None]).T @ Y
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_matches_scipy_real_form():
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        d = rng.normal(size=3); d /= np.linalg.norm(d)
+        theta = math.acos(d[2]); phi = math.atan2(d[1], d[0])
+        Y = O.sh_basis(d)[0]
+        for l in range(4):
+            for m in range(-l, l + 1):
+                c = complex(sp.sph_harm_y(l, abs(m), theta, phi))
+                if m > 0:
+                    ref = math.sqrt(2) * c.real
+                elif m < 0:
+                    ref = math.sqrt(2) * c.imag
+                else:
+                    ref = c.real
+                assert Y[l * l + l + m] == pytest.approx(ref, abs=1e-12)
+
+
+def test_sh_gradient_fd():
+    rng = np.random.default_rng(2)
+    d = rng.normal(size=3)
+    _, dY = O.sh_basis(d)
+    for k in range(3):
+        e = np.zeros(3); e[k] = 1e-6
+        fd = (O.sh_basis(d + e)[0] - O.sh_basis(d - e)[0]) / 2e-6
+        np.testing.assert_allclose(dY[:, k], fd, atol=1e-7)
+
+
+# --------------------------------------------------------------------------
+# a8: loss pins (Eq. 10-12)
+# --------------------------------------------------------------------------
+def _ssim_scipy(x, y):
+    nd = pytest.importorskip("scipy.ndimage")
+    g = np.exp(-((np.arange(11) - 5) ** 2) / (2 * 1.5 ** 2)); g /= g.sum()
+    w = np.outer(g, g)
+    f = lambda a: nd.correlate(a, w, mode="constant", cval=0.0)
+    out = []
+    for ch in range(x.shape[0]):
+        a, b = x[ch], y[ch]
+        mx, my = f(a), f(b)
+        sx, sy, sxy = f(a * a) - mx * mx, f(b * b) - my * my, f(a * b) - mx * my
+        C1, C2 = 0.01 ** 2, 0.03 ** 2
+        out.append(((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sx + sy + C2)))
+    return np.array(out)
+
+
+def test_ssim_matches_library_correlate():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (3, 23, 31)); y = np.clip(x + rng.normal(0, 0.1, x.shape), 0, 1)
+    lidar = np.zeros((23, 31))
+    terms, _, _ = O.loss(x, y, np.zeros((23, 31)), lidar, 1.0, 0.0, grads=False)
+    assert terms[2] == pytest.approx(_ssim_scipy(x, y).mean(), abs=1e-13)
+
+
+def test_ssim_identity_and_constant_closed_form():
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, (3, 20, 20))
+    terms, d_img, _ = O.loss(x, x, np.zeros((20, 20)), np.zeros((20, 20)), 1.0, 0.0)
+    assert terms[0] == pytest.approx(0.0, abs=1e-14)
+    assert np.abs(d_img).max() < 1e-14
+    # constant images a, b: interior pixels have SSIM (2ab + C1) / (a^2 + b^2 + C1)
+    a, b = 0.3, 0.7
+    xs, ys = np.full((3, 30, 30), a), np.full((3, 30, 30), b)
+    smap = _ssim_scipy(xs, ys)
+    expect = (2 * a * b + 1e-4) / (a * a + b * b + 1e-4)
+    np.testing.assert_allclose(smap[:, 5:-5, 5:-5], expect, rtol=1e-12)
+
+
+def test_l1_and_depth_terms_closed_form():
+    x = np.zeros((3, 2, 2)); y = np.zeros((3, 2, 2)); y[0, 0, 0] = 0.6; y[2, 1, 1] = -0.3
+    depth = np.array([[1.0, 2.0], [3.0, 4.0]]); lidar = np.array([[0.0, 2.5], [1.0, 0.0]])
+    terms, d_img, d_depth = O.loss(x, y, depth, lidar, 0.0, 0.5)
+    assert terms[1] == pytest.approx(0.9 / 12)
+    assert terms[3] == pytest.approx((0.5 + 2.0) / 2)
+    assert terms[0] == pytest.approx(0.9 / 12 + 0.5 * 1.25)
+    assert d_img[0, 0, 0] == pytest.approx(-1 / 12) and d_img[2, 1, 1] == pytest.approx(1 / 12)
+    assert d_img[1, 0, 0] == 0.0  # sign(0) = 0
+    np.testing.assert_allclose(d_depth, [[0, -0.25], [0.25, 0]])
+
+
+def test_loss_gradient_fd():
+    rng = np.random.default_rng(6)
+    H, W = 14, 17
+    x = rng.uniform(0, 1, (3, H, W)); y = rng.uniform(0, 1, (3, H, W))
+    depth = rng.uniform(2, 6, (H, W)); lidar = np.where(rng.uniform(size=(H, W)) < 0.3, rng.uniform(2, 6, (H, W)), 0)
+    _, d_img, d_depth = O.loss(x, y, depth, lidar, 0.2, 0.1)
+    eps = 1e-6
+    for (ch, i, j) in [(0, 0, 0), (1, 5, 7), (2, 13, 16), (0, 7, 3), (2, 2, 11)]:
+        xp, xm = x.copy(), x.copy(); xp[ch, i, j] += eps; xm[ch, i, j] -= eps
+        fd = (O.loss(xp, y, depth, lidar, 0.2, 0.1, False)[0][0] - O.loss(xm, y, depth, lidar, 0.2, 0.1, False)[0][0]) / (2 * eps)
+        assert d_img[ch, i, j] == pytest.approx(fd, rel=1e-6, abs=1e-11)
+    for (i, j) in zip(*np.nonzero(lidar)):
+        dp, dm = depth.copy(), depth.copy(); dp[i, j] += eps; dm[i, j] -= eps
+        fd = (O.loss(x, y, dp, lidar, 0.2, 0.1, False)[0][0] - O.loss(x, y, dm, lidar, 0.2, 0.1, False)[0][0]) / (2 * eps)
+        assert d_depth[i, j] == pytest.approx(fd, rel=1e-6)
+        break
+
+
+# --------------------------------------------------------------------------
+# a9: pyramid
+# --------------------------------------------------------------------------
+def test_pyramid_box_and_valid_mean():
+    rng = np.random.default_rng(7)
+    rgb = rng.uniform(size=(3, 8, 12))
+    depth = np.where(rng.uniform(size=(8, 12)) < 0.4, rng.uniform(1, 9, (8, 12)), 0.0)
+    r1, d1 = O.pyramid_down(rgb, depth)
+    np.testing.assert_allclose(r1, rgb.reshape(3, 4, 2, 6, 2).mean((2, 4)), rtol=1e-15)
+    blk = depth.reshape(4, 2, 6, 2).transpose(0, 2, 1, 3).reshape(4, 6, 4)
+    cnt = (blk > 0).sum(-1)
+    expect = np.where(cnt > 0, blk.sum(-1) / np.maximum(cnt, 1), 0.0)
+    np.testing.assert_allclose(d1, expect, rtol=1e-15)
+    rc, dc = O.pyramid(np.full((3, 16, 16), 0.37), np.full((16, 16), 5.0), 2)
+    np.testing.assert_allclose(rc, 0.37, rtol=1e-15); np.testing.assert_allclose(dc, 5.0)
+
+
+def test_level_camera_aligns_block_centres():
+    spec = S.identity_camera(1280, 1024, 860.0)
+    cam0 = cam_of(spec)
+    params, _, _, _ = S.small_scene(n=50)
+    pre0 = O.preprocess(params, cam0)
+    for lvl in (1, 2):
+        cam = O.level_camera(cam0, lvl)
+        assert (cam.W, cam.H) == (1280 >> lvl, 1024 >> lvl)
+        pre = O.preprocess(params, cam)
+        k = 2 ** lvl
+        # a level-l pixel p covers level-0 pixels k p .. k p + k - 1 (centre k p + (k-1)/2)
+        np.testing.assert_allclose(pre["uv"], (pre0["uv"] - (k - 1) / 2) / k, rtol=1e-6, atol=1e-5)
+
+
+# --------------------------------------------------------------------------
+# a6 + a7: hand-derived gradients against central finite differences
+# --------------------------------------------------------------------------
+def _fd_scene():
+    rng = np.random.default_rng(11)
+    n = 64
+    means = np.stack([rng.uniform(-0.9, 0.9, n), rng.uniform(-0.9, 0.9, n), rng.uniform(3, 6, n)], 1)
+    K = 16
+    sh = np.zeros((n, K, 3), np.float32)
+    sh[:, 0, :] = (rng.uniform(0.25, 0.75, (n, 3)) - 0.5) * math.sqrt(4 * math.pi)
+    sh[:, 1:, :] = rng.normal(0, 0.1, (n, K - 1, 3))
+    params = dict(means=means.astype(np.float32),
+                  log_scales=rng.normal(-2.2, 0.3, (n, 3)).astype(np.float32),
+                  quats=S.random_quats(rng, n), opacity_logits=rng.normal(0, 1, n).astype(np.float32),
+                  sh=sh, sh_degree=3)
+    R = _quat_R(np.array([1.0, 0.05, -0.03, 0.02])).astype(np.float32)
+    cam = O.Camera(R, np.array([0.05, -0.02, 0.1], np.float32), 40.0, 40.0, 16.0, 16.0, 32, 32)
+    gt = rng.uniform(0, 1, (3, 32, 32))
+    lidar = np.where(rng.uniform(size=(32, 32)) < 0.2, rng.uniform(3, 6, (32, 32)), 0.0)
+    return params, cam, gt, lidar
+
+
+def _loss_of(params, cam, gt, lidar):
+    r = O.render_view(params, cam, 0)
+    terms, _, _ = O.loss(r["rgb"], gt, r["depth"], lidar, 0.2, 0.1, grads=False)
+    return terms[0], r
+
+
+def test_backward_matches_central_fd():
+    params, cam, gt, lidar = _fd_scene()
+    out, grads = O.train_step(params, [cam], [0], [gt], [lidar], 0.2, 0.1)
+    base = out[0]["render"]
+    assert (base["pre"]["tiles"] > 0).sum() > 40
+    eps = 1e-4
+    names = ["means", "log_scales", "quats", "opacity_logits", "sh"]
+    rng = np.random.default_rng(12)
+    visible = np.nonzero(base["pre"]["tiles"] > 0)[0]
+    sh_gids = rng.choice(visible, 8, replace=False)
+    n_checked = n_skipped = 0
+    worst = 0.0
+    for name in names:
+        g_all = grads[name]
+        scale = np.abs(g_all).max()
+        for gi in (sh_gids if name == "sh" else visible):
+            flat_idx = range(int(np.prod(params[name].shape[1:])))
+            for k in flat_idx:
+                pp, pm = {k2: (v.copy() if isinstance(v, np.ndarray) else v) for k2, v in params.items()}, \
+                         {k2: (v.copy() if isinstance(v, np.ndarray) else v) for k2, v in params.items()}
+                ap = pp[name].reshape(params[name].shape[0], -1)
+                am = pm[name].reshape(params[name].shape[0], -1)
+                ap[gi, k] += np.float32(eps)
+                am[gi, k] -= np.float32(eps)
+                h = float(ap[gi, k]) - float(am[gi, k])
+                lp, rp = _loss_of(pp, cam, gt, lidar)
+                lm, rm = _loss_of(pm, cam, gt, lidar)
+                # same tile lists in the same order (the depth bits of the keys may move)
+                same = (np.array_equal(rp["keys"] >> np.uint64(32), rm["keys"] >> np.uint64(32))
+                        and np.array_equal(rp["vals"], rm["vals"])
+                        and np.array_equal(rp["signature"], rm["signature"])
+                        and np.array_equal(rp["signature"], base["signature"])
+                        # nor may an L1 term change sign (its kink)
+                        and np.array_equal(np.sign(rp["rgb"] - gt), np.sign(rm["rgb"] - gt))
+                        and np.array_equal(np.sign(rp["depth"] - lidar), np.sign(rm["depth"] - lidar)))
+                if not same:
+                    n_skipped += 1
+                    continue
+                fd = (lp - lm) / h
+                an = g_all.reshape(params[name].shape[0], -1)[gi, k]
+                err = abs(fd - an) / (abs(an) + 1e-3 * scale + 1e-12)
+                worst = max(worst, err)
+                assert err < 2e-5, (name, gi, k, fd, an)
+                n_checked += 1
+    # a perturbation that flips any threshold test anywhere in the image is skipped
+    assert n_checked > 900 and n_skipped < 0.1 * (n_checked + n_skipped)
