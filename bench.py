@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the LVI-GS differentiable splatting hot path on GB300.
+
+One step = every row of the hot path over one batch of keyframes: target
+pyramid (a9), preprocess (a1), key expansion and sorts (a2-a4), forward
+compositing (a5), fused L1 + SSIM + LiDAR-depth loss (a8), backward
+compositing (a6) and the chain rule to all parameters (a7), for 8 keyframes
+at mixed pyramid levels sharing 1M Gaussians (SH degree 3), replayed as one
+CUDA graph.  The same work is also timed as 8 sequential plain single-view
+calls, end to end through the public API with host targets, and (on the CPU)
+with the FP64 oracle on a bounded sample.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an
+independent replica of the step on its own GPU (no collective on the data
+path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd train steps/s & Mpix/s (1M Gaussians, 1280x1024), batched vs plain"
+WORKLOAD = "lidar_1000000_8v"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(gpu_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 2070.0, "fallback"
+
+
+def algorithmic_bytes(N, V, K, n_vis, M, P, loaded):
+    """Bytes each phase must move (float32 = 4 B), from the step's counts."""
+    prm = N * 4 * (11 + 3 * K)
+    return {
+        "preprocess": prm + V * N * 16 + n_vis * 48,
+        "compact": V * N * 8 + n_vis * 8,
+        "depth_sort": 4 * 20 * n_vis,
+        "offsets": n_vis * 12,
+        "emit": n_vis * 16 + M * 8,
+        "tile_sort": 2 * 20 * M,
+        "ranges": M * 4,
+        "composite_fwd": loaded * 52 + P * 28,
+        "loss": P * (32 + 36 + 36 + 32 + 16),
+        "composite_bwd": loaded * 52 + P * 40,
+        "preprocess_bwd": 2 * prm + n_vis * 52,
+    }
+
+
+def alu_flops(n_contrib_sum):
+    # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernels:
+    # forward ~20 (offset, quadratic form, alpha, transmittance, 4 accumulations),
+    # backward ~70 (the same plus dL/dalpha, five suffix sums, ten partials and
+    # a 5-level shuffle sum of 10 values amortised over 32 lanes)
+    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 70.0 * n_contrib_sum}
+
+
+def run_ours(args):
+    import torch
+
+    import synthetic as S
+    import paper_2411_02703_gb300 as P
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tile = tuple(int(x) for x in args.tile.split("x"))
+    wl = S.workload(args.workload)
+    params = wl["params"]
+    cams, levels = wl["cams"], wl["levels"]
+    lam, lamd = wl["lam"], wl["lam_d"]
+    dev = {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) else v)
+           for k, v in params.items()}
+    gts = [torch.from_numpy(g).cuda() for g in wl["gts"]]
+    lis = [torch.from_numpy(g).cuda() for g in wl["lidars"]]
+    gts_h = [torch.from_numpy(g).pin_memory() for g in wl["gts"]]
+    lis_h = [torch.from_numpy(g).pin_memory() for g in wl["lidars"]]
+    lv = P.Context(tile=tile)
+    grads = {k: torch.zeros_like(dev[k]) for k in P.PARAM_NAMES}
+    N = params["means"].shape[0]
+    V = len(cams)
+    K = params["sh"].shape[1]
+    pix = sum((c.W >> l) * (c.H >> l) for c, l in zip(cams, levels))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def step():
+        lv.train_step_batched(dev, cams, levels, gts, lis, lam, lamd, grads=grads)
+
+    # warm-up (first call sizes the workspace eagerly, the second captures the graph)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    lv.sync_status()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_uuid = str(local)
+    sampler = ClockSampler(gpu_uuid)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    lv.sync_status()
+    ms_batched = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    stats = lv.step_stats()
+    _, kernels_per_step = lv.profile_read()
+
+    # plain path: 8 sequential single-view calls (render, loss, backward) per step
+    ms_plain = None
+    if not args.skip_plain:
+        pgrads = {k: torch.zeros_like(dev[k]) for k in P.PARAM_NAMES}
+
+        def plain_step():
+            for i, (c, l) in enumerate(zip(cams, levels)):
+                g_l, d_l = gts[i], lis[i]
+                for _ in range(l):
+                    g_l, d_l = lv.pyramid_down(g_l, d_l)
+                rgb, depth, alpha, slot = lv.render(dev, c, l)
+                _, d_rgb, d_dep = lv.loss(rgb, depth, g_l, d_l, lam, lamd)
+                lv.backward(slot, dev, d_rgb, d_dep, grads=pgrads, accumulate=i > 0)
+                lv.release(slot)
+
+        for _ in range(2):
+            plain_step()
+        torch.cuda.synchronize()
+        kp = max(3, args.steps // 4)
+        barrier()
+        e0.record(stream)
+        for _ in range(kp):
+            plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_plain = max_over_ranks(e0.elapsed_time(e1) / kp)
+
+    # per-phase device time of the same step enqueued eagerly (events per phase)
+    lv.profile(True)
+    kprof = 5
+    for _ in range(kprof):
+        lv.train_step_batched(dev, cams, levels, gts, lis, lam, lamd, grads=grads, graph=False)
+    torch.cuda.synchronize()
+    phases, _ = lv.profile_read()
+    lv.profile(False)
+    phase_ms = {k: v[0] / kprof for k, v in phases.items()}  # ms per step
+
+    # end to end through the public API: pinned host targets in, losses out, every step
+    for _ in range(2):
+        lv.train_step_batched(dev, cams, levels, gts_h, lis_h, lam, lamd, grads=grads, host_targets=True,
+                              host_loss=True)
+    ke = max(5, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        lv.train_step_batched(dev, cams, levels, gts_h, lis_h, lam, lamd, grads=grads, host_targets=True,
+                              host_loss=True)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / ke)
+    h2d = sum(g.numel() * 4 for g in gts_h) + sum(x.numel() * 4 for x in lis_h)
+    d2h = V * 4 * 8
+
+    n_vis, M, nc_sum, P_px = stats
+    # instances the compositing kernels gather: bounded by M; use M (upper bound)
+    ab = algorithmic_bytes(N, V, K, n_vis, M, P_px, M)
+    flops = alu_flops(nc_sum)
+    hbm_peak, sm_max, peak_kind = peaks()
+    dominant = max(phase_ms, key=lambda k: phase_ms[k])
+    t_dom = phase_ms[dominant] / 1e3
+    if dominant in flops:
+        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
+        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": dominant, "achieved": flops[dominant] / t_dom / 1e12,
+                "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": None,
+                "peak_source": "152 SM x 128 FP32 lanes x 2 x sm_max_mhz",
+                "hbm_achieved_gbs": ab[dominant] / t_dom / 1e9}
+    else:
+        ach = ab[dominant] / t_dom / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
+
+    steps_per_s = 1000.0 / ms_batched
+    value = world * steps_per_s
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "train steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_batched, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded LiDAR-sweep scene and procedural targets)",
+        "config": {"workload": args.workload, "gaussians": N, "views": V, "levels": levels,
+                   "base_resolution": "1280x1024", "sh_degree": int(params["sh_degree"]), "tile": args.tile,
+                   "loss": "0.8 L1 + 0.2 (1-SSIM) + 0.1 depth L1", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (236 MB of parameters per step)"},
+        "mpix_per_s": round(world * pix * steps_per_s / 1e6, 3),
+        "plain_ms_per_step": None if ms_plain is None else round(ms_plain, 4),
+        "batched_vs_plain": None if ms_plain is None else round(ms_plain / ms_batched, 3),
+        "e2e": {"value": round(world / t_e2e, 4), "unit": "train steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(kernels_per_step) * args.steps,
+        "roofline": roof,
+        "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+        "counts": {"visible_pairs": n_vis, "instances": M, "contrib_sum": nc_sum, "pixels": P_px},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.skip_cpu:
+        out["cpu_baseline"] = cpu_baseline(wl, pix)
+    lv.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(wl, pix_total, budget_s=25.0):
+    """The oracle as it stands, on the host cores, over a bounded sample of the step.
+
+    Sample: the views of the step in order, each a full oracle pass (pyramid,
+    render, loss, backward) at its level, until about `budget_s` of CPU work;
+    the step time is extrapolated by pixel count.
+    """
+    import oracle as O
+
+    t0 = time.perf_counter()
+    done_px = 0
+    done = []
+    for i, (c, l) in enumerate(zip(wl["cams"], wl["levels"])):
+        cam = O.Camera(c.R, c.t, c.fx, c.fy, c.cx, c.cy, c.W, c.H)
+        O.train_step(wl["params"], [cam], [l], [wl["gts"][i]], [wl["lidars"][i]], wl["lam"], wl["lam_d"])
+        done_px += (c.W >> l) * (c.H >> l)
+        done.append(f"view {i} (level {l})")
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t = time.perf_counter() - t0
+    step_s = t * pix_total / done_px
+    return {"value": round(1.0 / step_s, 6), "unit": "train steps/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{', '.join(done)} of the 8-view step, {t:.1f} s, extrapolated by pixel count"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import synthetic as S
+
+    wl = S.workload(args.workload)
+    pix = sum((c.W >> l) * (c.H >> l) for c, l in zip(wl["cams"], wl["levels"]))
+    vals = []
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(wl, pix, budget_s=5.0)
+    cb = None
+    for _ in range(max(1, min(args.steps, 3))):
+        cb = cpu_baseline(wl, pix, budget_s=20.0)
+        vals.append(cb["value"])
+    v = float(np.median(vals))
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "train steps/s", "n_gpus": 1,
+           "steps": len(vals), "warmup": min(args.warmup, 1), "ms_per_step": 1000.0 / v,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded LiDAR-sweep scene and procedural targets)",
+           "config": {"workload": args.workload, "implementation": "FP64 CPU oracle (oracle/)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "train steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

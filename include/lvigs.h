@@ -1,0 +1,236 @@
+/*
+ * lvigs.h -- C ABI of the GB300 (sm_103a) differentiable Gaussian-splatting
+ * hot path of LVI-GS (arxiv 2411.02703).
+ *
+ * The library renders colour, depth and visibility images from a set of 3D
+ * Gaussians seen by a pinhole camera at a pyramid level (Sec. III-B,
+ * Eq. (2)-(7); Sec. III-D), evaluates the mapping loss (Sec. III-E,
+ * Eq. (10)-(12)) and returns the gradient of a loss with respect to every
+ * Gaussian parameter (means, log-scales, quaternions, opacity logits and
+ * spherical-harmonic coefficients; the parameter set of Sec. III-E).
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer to image, parameter or gradient data is a DEVICE pointer
+ *     into memory the caller owns (contiguous, float32, layouts below), unless
+ *     a flag says otherwise.  The library owns only its workspace.
+ *   - Work is enqueued on the CUDA stream passed as `stream` (a cudaStream_t;
+ *     NULL is the legacy default stream) and runs asynchronously.  Argument
+ *     errors are returned before anything is enqueued.  Errors found on the
+ *     device are latched in the context and returned by lvigs_sync_status().
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - Fixed constants of the method (readings of the paper, which is silent
+ *     on them): near plane 0.2, 0.3 px^2 dilation of the projected
+ *     covariance, Jacobian clamp at 1.3 x tan(half field of view), radius
+ *     ceil(3 sqrt(lambda_max)) with the eigenvalue discriminant floored at
+ *     0.1, alpha clamp 0.99, alpha cut-off 1/255, compositing stops before a
+ *     Gaussian that would take the transmittance below 1e-4, black
+ *     background, view-space z as the depth d_i of Eq. (4), real spherical
+ *     harmonics up to degree 3 plus 0.5, clamped at 0.
+ *
+ * Layouts
+ *   means [n,3], log_scales [n,3], quats [n,4] (w,x,y,z; normalised inside),
+ *   opacity_logits [n] (opacity = sigmoid), sh [n, sh_stride_k, 3];
+ *   images are planar: rgb [3,H,W], depth [H,W], alpha [H,W].
+ */
+#ifndef LVIGS_H
+#define LVIGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LVIGS_MAX_VIEWS 32 /* views per batched call */
+#define LVIGS_MAX_LEVEL 4  /* pyramid levels 0..4 */
+
+typedef enum {
+    LVIGS_OK = 0,
+    LVIGS_ERR_INVALID_ARG = 1,   /* a NULL, size, level or layout outside the contract */
+    LVIGS_ERR_OUT_OF_MEMORY = 2, /* workspace allocation failed */
+    LVIGS_ERR_CUDA = 3,          /* a CUDA runtime call failed (see lvigs_last_error) */
+    LVIGS_ERR_CAPACITY = 4,      /* workspace cap or instance capacity exceeded */
+    LVIGS_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    LVIGS_ERR_STATE = 6          /* a view slot that is free, stale or of another context */
+} lvigs_status;
+
+typedef struct lvigs_ctx lvigs_ctx;
+
+/* Context configuration.  Tile size changes which Gaussians a pixel composites
+ * (a pixel composites every Gaussian whose tile rectangle covers its tile), so
+ * results depend on it; batch_depth does not change results. */
+typedef struct {
+    int tile_w, tile_h;         /* 16x16 (default), 8x8 or 32x16 */
+    int batch_depth;            /* Gaussians staged in shared memory per round; 0 = auto */
+    size_t max_workspace_bytes; /* 0 = no cap; else LVIGS_ERR_CAPACITY beyond it */
+} lvigs_config;
+
+/* Gaussian map (device pointers, caller-owned, float32). */
+typedef struct {
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+    int64_t n;       /* number of Gaussians, 0 <= n < 2^31 */
+    int sh_degree;   /* active SH degree 0..3 (Sec. III-E schedule) */
+    int sh_stride_k; /* coefficients per Gaussian in `sh`, >= (sh_degree+1)^2 */
+} lvigs_gaussians;
+
+/* Pinhole camera at pyramid level 0.  R, t map world to camera coordinates
+ * (x right, y down, z forward): the pose [Q_iw, T_iw] of Eq. (7). */
+typedef struct {
+    float R[9]; /* row-major */
+    float t[3];
+    float fx, fy, cx, cy;
+    int width, height;
+} lvigs_camera;
+
+/* Render outputs (device, caller-owned; sized for the level's W x H). */
+typedef struct {
+    float *rgb;   /* [3,H,W]  C_p of Eq. (3) */
+    float *depth; /* [H,W]    D_p of Eq. (4) */
+    float *alpha; /* [H,W]    V_p of Eq. (5) */
+} lvigs_image_out;
+
+/* Parameter gradients (device, caller-owned, same layouts as the parameters).
+ * accumulate = 0 overwrites, 1 adds to the current contents. */
+typedef struct {
+    float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_sh;
+    int accumulate;
+} lvigs_grads;
+
+/* Flags of a batched step. */
+#define LVIGS_STEP_HOST_TARGETS 1 /* gt_rgb / lidar_depth are pinned HOST pointers, copied in */
+#define LVIGS_STEP_HOST_LOSS 2    /* losses is a HOST pointer; the call waits for the step */
+#define LVIGS_STEP_NO_GRAPH 4     /* enqueue kernels directly instead of replaying a CUDA graph */
+
+/* One batched training step over several keyframes at mixed pyramid levels. */
+typedef struct {
+    int n_views;                     /* 1..LVIGS_MAX_VIEWS */
+    const lvigs_camera *cameras;     /* host array [n_views], level-0 cameras */
+    const int *levels;               /* host array [n_views], 0..LVIGS_MAX_LEVEL */
+    const float *const *gt_rgb;      /* host array of n_views pointers to level-0 [3,H0,W0] */
+    const float *const *lidar_depth; /* host array of n_views pointers to level-0 [H0,W0]; 0 = no return */
+    float lambda_ssim;               /* lambda of Eq. (11) */
+    float lambda_depth;              /* lambda_d of Eq. (10) */
+    int flags;                       /* LVIGS_STEP_* */
+    double *losses;                  /* [n_views,4]: total, L1, mean SSIM, depth L1 */
+    float *const *rgb_out;           /* optional host array of n_views device pointers, or NULL */
+    float *const *depth_out;         /* optional, as rgb_out */
+    float *const *alpha_out;         /* optional, as rgb_out */
+} lvigs_batch;
+
+/* ----------------------------------------------------------------------- */
+
+/* Library version string (static storage). */
+const char *lvigs_version(void);
+
+/* Default configuration (16x16 tiles, automatic batch depth, no cap). */
+void lvigs_config_default(lvigs_config *cfg);
+
+/* Create a context on the current CUDA device.  cfg may be NULL (defaults).
+ * Returns LVIGS_ERR_INVALID_ARG for an unsupported tile size. */
+lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg);
+
+/* Destroy a context and free its workspace (synchronises the device). */
+void lvigs_destroy(lvigs_ctx *ctx);
+
+/* Image size of pyramid level `level` of a level-0 camera: W >> level, H >> level. */
+lvigs_status lvigs_level_size(const lvigs_camera *cam, int level, int *width, int *height);
+
+/* Forward render of one view at pyramid level `level` (Sec. III-B, Eq. (2)-(7);
+ * Sec. III-D).  Writes out->rgb/depth/alpha at the level's size and returns
+ * in *view_slot a handle of the compositing state kept for lvigs_backward.
+ * The parameter buffers must stay unchanged until the backward call.  This
+ * call waits once on the stream to learn the number of (tile, Gaussian)
+ * instances and size the workspace. */
+lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam,
+                          int level, const lvigs_image_out *out, int *view_slot, void *stream);
+
+/* Gradients of a loss with respect to the Gaussian parameters, given the
+ * gradients of that loss with respect to the images of `view_slot`
+ * (dL_dalpha may be NULL).  Reverse traversal of each pixel's list with the
+ * transmittance recovered by division (no per-Gaussian state is stored). */
+lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
+                            const float *dL_ddepth, const float *dL_dalpha,
+                            const lvigs_grads *grads, void *stream);
+
+/* Mapping loss of Eq. (10)-(12) for one W x H image:
+ *   L = (1 - lambda) L1(rgb, gt) + lambda (1 - mean SSIM) + lambda_d L_d,
+ * SSIM with an 11x11 Gaussian window (sigma 1.5), zero padding,
+ * C1 = 0.01^2, C2 = 0.03^2, averaged over channels and pixels; L_d is the
+ * mean |depth - lidar| over pixels with lidar > 0 (0 if none).
+ * loss_out: 4 device doubles (total, L1, mean SSIM, L_d).  d_rgb / d_depth
+ * receive dL/drgb and dL/ddepth (either may be NULL to skip gradients). */
+lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
+                        const float *depth, const float *gt_rgb, const float *lidar_depth,
+                        float lambda_ssim, float lambda_depth, double *loss_out, float *d_rgb,
+                        float *d_depth, void *stream);
+
+/* One pyramid level down (Sec. III-D): rgb 2x2 box mean, depth the mean of
+ * the valid (> 0) samples of each 2x2 block (0 if none).  Output size is
+ * (width/2) x (height/2). */
+lvigs_status lvigs_pyramid_down(int width, int height, const float *rgb, const float *depth,
+                                float *rgb_out, float *depth_out, void *stream);
+
+/* Batched training step: every view rendered, its loss evaluated against its
+ * level of the target pyramid and differentiated, gradients accumulated over
+ * views into `grads`, all in one CUDA graph (unless LVIGS_STEP_NO_GRAPH).
+ * Returns after enqueueing (or after the step with LVIGS_STEP_HOST_LOSS).
+ * Device-side capacity overflow is reported by lvigs_sync_status; the
+ * capacity grows for the next call. */
+lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gaussians *g,
+                                      const lvigs_batch *batch, const lvigs_grads *grads,
+                                      void *stream);
+
+/* Parity hooks: the sorted 64-bit keys ((tile id << 32) | float bits of depth)
+ * and Gaussian indices of `view_slot`.  With keys == NULL only *m is set.
+ * keys/vals are device pointers with room for *m entries on input (m_cap). */
+lvigs_status lvigs_debug_keys(lvigs_ctx *ctx, int view_slot, uint64_t *keys, uint32_t *vals,
+                              int64_t m_cap, int64_t *m, void *stream);
+
+/* Parity hook: per-tile [start, end) of the sorted list (device uint32 [n_tiles,2])
+ * and the per-pixel contributor count and final transmittance (device). */
+lvigs_status lvigs_debug_state(lvigs_ctx *ctx, int view_slot, uint32_t *ranges, int32_t *n_contrib,
+                               float *final_T, int *n_tiles, void *stream);
+
+/* Wait for `stream` and return any error latched on the device since the
+ * last call (capacity overflow, bounded-wait timeout), clearing it. */
+lvigs_status lvigs_sync_status(lvigs_ctx *ctx, void *stream);
+
+/* Release a view slot (its state becomes stale). */
+lvigs_status lvigs_release_view(lvigs_ctx *ctx, int view_slot);
+
+/* Last error message of the context (static storage of the context). */
+const char *lvigs_last_error(const lvigs_ctx *ctx);
+
+/* Opt-in device timing of eagerly enqueued work (not of graph replays):
+ * CUDA events around each phase below, on the stream the phase runs on. */
+enum {
+    LVIGS_PHASE_PREPROCESS = 0,     /* a1 */
+    LVIGS_PHASE_COMPACT = 1,        /* visibility scan + compaction */
+    LVIGS_PHASE_DEPTH_SORT = 2,     /* a3, depth radix sort of visible Gaussians */
+    LVIGS_PHASE_OFFSETS = 3,        /* a2, scan of tiles touched */
+    LVIGS_PHASE_EMIT = 4,           /* a2, instance emission */
+    LVIGS_PHASE_TILE_SORT = 5,      /* a3, tile-id radix sort of instances */
+    LVIGS_PHASE_RANGES = 6,         /* a4 */
+    LVIGS_PHASE_COMPOSITE_FWD = 7,  /* a5 */
+    LVIGS_PHASE_LOSS = 8,           /* a8 */
+    LVIGS_PHASE_COMPOSITE_BWD = 9,  /* a6 */
+    LVIGS_PHASE_PREPROCESS_BWD = 10,/* a7 */
+    LVIGS_PHASE_PYRAMID = 11,       /* a9 */
+    LVIGS_N_PHASES = 12
+};
+lvigs_status lvigs_profile_enable(lvigs_ctx *ctx, int enable);
+/* Waits for the recorded phases; writes the summed milliseconds and call
+ * counts per phase (arrays of LVIGS_N_PHASES, either may be NULL) and the
+ * kernel launches per replay of the batched-step graph, then resets. */
+lvigs_status lvigs_profile_read(lvigs_ctx *ctx, double *ms, int64_t *calls, int *kernels_per_step);
+
+/* Work counts of the last batched step (waits on `stream`): out[0] visible
+ * (view, Gaussian) pairs, out[1] (tile, Gaussian) instances, out[2] the sum
+ * over pixels of the contributor counts, out[3] pixels rendered. */
+lvigs_status lvigs_step_stats(lvigs_ctx *ctx, int64_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LVIGS_H */

@@ -1,0 +1,963 @@
+// api.cu -- the C ABI of include/lvigs.h: contexts and their workspace, the
+// plain single-view path (render / loss / backward), the batched path that
+// replays one CUDA graph per step, and the parity hooks.
+//
+// Host arithmetic that feeds the tile keys (the pyramid-level intrinsics and
+// the Jacobian clamp limits) is plain binary32 C++ compiled with
+// -ffp-contract=off, one rounding per operation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lvigs.h"
+#include "lvigs_internal.cuh"
+
+using namespace lvigs;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct RenderState {
+    DevBuf recs, tiles, zbits, rects;
+    DevBuf inst_a_t, inst_a_v, inst_b_t, inst_b_v;
+    DevBuf ranges, final_T, n_contrib, vs_dev, counters;
+    ViewSet vs{};
+    GaussParams P{};
+    int64_t m = 0;      // instances of the last eager build
+    int64_t m_cap = 0;  // instance capacity
+    int sorted_in_b = 0;
+    bool valid = false;
+    uint32_t generation = 0;
+
+    const uint32_t *sorted_tiles() const { return (const uint32_t *)(sorted_in_b ? inst_b_t.p : inst_a_t.p); }
+    const uint32_t *sorted_vals() const { return (const uint32_t *)(sorted_in_b ? inst_b_v.p : inst_a_v.p); }
+};
+
+struct BatchKey {
+    std::vector<uint64_t> k;
+    bool operator==(const BatchKey &o) const { return k == o.k; }
+};
+
+} // namespace
+
+struct lvigs_ctx {
+    lvigs_config cfg{};
+    int device = 0;
+    std::string err;
+    size_t bytes_in_use = 0;
+    uint64_t ws_epoch = 0;
+    bool capturing = false;
+    bool capture_short = false;
+
+    // shared temporaries (one stream at a time per context)
+    DevBuf pos, ck, cv, ck2, cv2, scan_tmp, radix_tmp, status, g2d, loss_tmp, stats;
+    uint32_t *host_counters = nullptr; // pinned [4]
+    uint32_t *host_status = nullptr;   // pinned [1]
+
+    std::vector<RenderState *> slots;
+
+    // batched path
+    RenderState batch;
+    DevBuf gt_stage[kMaxViews], lidar_stage[kMaxViews];
+    DevBuf pyr_rgb[kMaxViews][LVIGS_MAX_LEVEL + 1], pyr_depth[kMaxViews][LVIGS_MAX_LEVEL + 1];
+    DevBuf img_rgb, img_depth, img_alpha, d_rgb, d_depth, losses_dev;
+    double *host_losses = nullptr;       // pinned [kMaxViews * 4]
+    uint32_t *host_batch_counters = nullptr; // pinned [4]
+    ViewSet *vs_staging = nullptr;       // pinned
+    cudaEvent_t vs_event = nullptr, step_event = nullptr;
+    bool step_pending = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    BatchKey graph_key;
+    bool graph_ok = false;
+    int kernels_per_step = 0;
+
+    // opt-in per-phase device timing of eagerly enqueued work
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    double prof_ms[LVIGS_N_PHASES] = {};
+    int64_t prof_calls[LVIGS_N_PHASES] = {};
+};
+
+namespace {
+
+lvigs_status fail(lvigs_ctx *c, lvigs_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+lvigs_status cuda_fail(lvigs_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, LVIGS_ERR_CUDA, m);
+}
+
+#define LV_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);             \
+    } while (0)
+
+// Grow a buffer to at least `bytes`.  While a graph is being captured no
+// allocation is allowed: a short buffer marks the capture as unusable.
+lvigs_status ensure(lvigs_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return LVIGS_OK;
+    if (ctx->capturing) {
+        ctx->capture_short = true;
+        return LVIGS_ERR_CAPACITY;
+    }
+    size_t want = bytes + bytes / 8;
+    want = (want + 255) / 256 * 256;
+    const size_t after = ctx->bytes_in_use - b.bytes + want;
+    if (ctx->cfg.max_workspace_bytes && after > ctx->cfg.max_workspace_bytes)
+        return fail(ctx, LVIGS_ERR_CAPACITY, "workspace cap exceeded");
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->bytes_in_use -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LVIGS_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b.p = p;
+    b.bytes = want;
+    ctx->bytes_in_use += want;
+    ++ctx->ws_epoch;
+    return LVIGS_OK;
+}
+
+void release(lvigs_ctx *ctx, DevBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->bytes_in_use -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void release_state(lvigs_ctx *ctx, RenderState &s) {
+    DevBuf *all[] = {&s.recs, &s.tiles, &s.zbits, &s.rects, &s.inst_a_t, &s.inst_a_v, &s.inst_b_t,
+                     &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters};
+    for (DevBuf *b : all) release(ctx, *b);
+    s.valid = false;
+    s.m_cap = 0;
+}
+
+// Records device time of one phase while profiling is on and nothing is captured.
+struct Phase {
+    lvigs_ctx *ctx;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t take() {
+        cudaEvent_t e;
+        if (!ctx->ev_pool.empty()) {
+            e = ctx->ev_pool.back();
+            ctx->ev_pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    Phase(lvigs_ctx *c, int ph, cudaStream_t st) : ctx(c), phase(ph), s(st) {
+        if (ctx->prof && !ctx->capturing) {
+            e0 = take();
+            e1 = take();
+            if (e0) cudaEventRecord(e0, s);
+        }
+    }
+    ~Phase() {
+        if (e0 && e1) {
+            cudaEventRecord(e1, s);
+            ctx->prof_pending.push_back({phase, {e0, e1}});
+        }
+    }
+};
+
+#define LV_TRY(expr)                                 \
+    do {                                             \
+        lvigs_status st_ = (expr);                   \
+        if (st_ != LVIGS_OK) return st_;             \
+    } while (0)
+
+bool tile_supported(int w, int h) {
+    return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 16);
+}
+
+// Level-l camera (Sec. III-D): the level halves the image l times; with pixels
+// sampled at integer coordinates a level-l pixel's block centre gives the
+// principal point (c + 0.5) / 2^l - 0.5.  Binary32, one rounding per op.
+ViewDesc make_view(const lvigs_camera &c, int level, int tw, int th) {
+    ViewDesc v{};
+    float scale = 1.0f;
+    for (int i = 0; i < level; ++i) scale = scale * 0.5f;
+    for (int i = 0; i < 9; ++i) v.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) v.t[i] = c.t[i];
+    v.fx = c.fx * scale;
+    v.fy = c.fy * scale;
+    v.cx = (c.cx + 0.5f) * scale - 0.5f;
+    v.cy = (c.cy + 0.5f) * scale - 0.5f;
+    v.W = c.width >> level;
+    v.H = c.height >> level;
+    v.limx = 1.3f * ((0.5f * (float)v.W) / v.fx);
+    v.limy = 1.3f * ((0.5f * (float)v.H) / v.fy);
+    for (int i = 0; i < 3; ++i)
+        v.campos[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
+    v.tiles_x = (v.W + tw - 1) / tw;
+    v.tiles_y = (v.H + th - 1) / th;
+    return v;
+}
+
+lvigs_status check_gauss(lvigs_ctx *ctx, const lvigs_gaussians *g) {
+    if (!g) return fail(ctx, LVIGS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0 || g->n >= (int64_t)1 << 31) return fail(ctx, LVIGS_ERR_INVALID_ARG, "n out of range");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, LVIGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->sh_stride_k < (g->sh_degree + 1) * (g->sh_degree + 1))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "sh_stride_k < (sh_degree+1)^2");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL parameter pointer");
+    return LVIGS_OK;
+}
+
+lvigs_status check_camera(lvigs_ctx *ctx, const lvigs_camera *cam, int level) {
+    if (!cam) return fail(ctx, LVIGS_ERR_INVALID_ARG, "camera is NULL");
+    if (level < 0 || level > LVIGS_MAX_LEVEL) return fail(ctx, LVIGS_ERR_INVALID_ARG, "level out of range");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 16384 || cam->height > 16384)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "image size out of range");
+    if ((cam->width >> level) < 1 || (cam->height >> level) < 1)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "level too deep for the image");
+    if (!(cam->fx > 0.f) || !(cam->fy > 0.f)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "focal length must be > 0");
+    return LVIGS_OK;
+}
+
+GaussParams to_params(const lvigs_gaussians *g) {
+    GaussParams P;
+    P.means = g->means;
+    P.log_scales = g->log_scales;
+    P.quats = g->quats;
+    P.opacity_logits = g->opacity_logits;
+    P.sh = g->sh;
+    P.n = (int)g->n;
+    P.sh_degree = g->sh_degree;
+    P.sh_stride_k = g->sh_stride_k;
+    return P;
+}
+
+int key_bits(uint32_t total_tiles) {
+    int b = 1;
+    while (b < 32 && ((uint64_t)1 << b) < total_tiles) ++b;
+    return b;
+}
+
+// a1-a4 for the views of `st`: preprocess, compact, depth sort, scan,
+// emit, tile sort, ranges.  In eager mode the call waits once to learn the
+// instance count and grows the instance buffers; otherwise it relies on
+// st.m_cap (overflow is latched in the status word).
+lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool eager, double headroom) {
+    const int64_t N = st.P.n;
+    const int64_t VN = N * st.vs.n_views;
+    LV_TRY(ensure(ctx, st.recs, (size_t)VN * sizeof(GRec)));
+    LV_TRY(ensure(ctx, st.tiles, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, st.zbits, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, st.rects, (size_t)VN * 8));
+    LV_TRY(ensure(ctx, st.counters, 16));
+    LV_TRY(ensure(ctx, st.ranges, (size_t)st.vs.total_tiles * sizeof(uint2)));
+    LV_TRY(ensure(ctx, ctx->pos, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, ctx->ck, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, ctx->cv, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, ctx->ck2, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, ctx->cv2, (size_t)VN * 4));
+    LV_TRY(ensure(ctx, ctx->scan_tmp, scan_tmp_words(VN) * 4));
+    LV_TRY(ensure(ctx, ctx->radix_tmp, radix_tmp_words((int64_t)1 << 40) * 4));
+    LV_TRY(ensure(ctx, ctx->status, 16));
+    if (!eager) {
+        LV_TRY(ensure(ctx, st.inst_a_t, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_a_v, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_b_t, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_b_v, (size_t)st.m_cap * 4));
+    }
+    uint32_t *cnt = (uint32_t *)st.counters.p; // [0] visible, [1] instances, [2] clamped
+    const ViewSet *vsd = (const ViewSet *)st.vs_dev.p;
+
+    {
+        Phase ph(ctx, LVIGS_PHASE_PREPROCESS, s);
+        launch_preprocess_fwd(st.P, vsd, (GRec *)st.recs.p, (uint32_t *)st.tiles.p, (uint32_t *)st.zbits.p,
+                              (uint2 *)st.rects.p, s);
+    }
+    {
+        Phase ph(ctx, LVIGS_PHASE_COMPACT, s);
+        launch_scan((const uint32_t *)st.tiles.p, nullptr, 1, (uint32_t *)ctx->pos.p, cnt + 0, nullptr, VN,
+                    (uint32_t *)ctx->scan_tmp.p, s);
+        launch_compact((const uint32_t *)st.tiles.p, (const uint32_t *)st.zbits.p, (const uint32_t *)ctx->pos.p,
+                       (uint32_t *)ctx->ck.p, (uint32_t *)ctx->cv.p, VN, s);
+    }
+    int r;
+    {
+        // depth keys of visible Gaussians are positive floats: 31 significant bits
+        Phase ph(ctx, LVIGS_PHASE_DEPTH_SORT, s);
+        r = launch_radix_sort((uint32_t *)ctx->ck.p, (uint32_t *)ctx->cv.p, (uint32_t *)ctx->ck2.p,
+                              (uint32_t *)ctx->cv2.p, cnt + 0, VN, 31, (uint32_t *)ctx->radix_tmp.p, s);
+    }
+    const uint32_t *sorted_idx = (const uint32_t *)(r ? ctx->cv2.p : ctx->cv.p);
+    {
+        Phase ph(ctx, LVIGS_PHASE_OFFSETS, s);
+        launch_scan((const uint32_t *)st.tiles.p, sorted_idx, 0, (uint32_t *)ctx->pos.p, cnt + 1, cnt + 0, VN,
+                    (uint32_t *)ctx->scan_tmp.p, s);
+    }
+    if (eager) {
+        LV_CUDA(cudaMemcpyAsync(ctx->host_counters, cnt, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        st.m = ctx->host_counters[1];
+        const int64_t need = (int64_t)((double)st.m * headroom) + 1024;
+        if (st.m_cap < st.m || st.m_cap < need / 2 || st.m_cap == 0) st.m_cap = need;
+        if (st.m_cap > 0xfffffff0LL) return fail(ctx, LVIGS_ERR_CAPACITY, "more than 2^32 instances");
+        LV_TRY(ensure(ctx, st.inst_a_t, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_a_v, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_b_t, (size_t)st.m_cap * 4));
+        LV_TRY(ensure(ctx, st.inst_b_v, (size_t)st.m_cap * 4));
+    }
+    {
+        Phase ph(ctx, LVIGS_PHASE_EMIT, s);
+        launch_emit(vsd, sorted_idx, (const uint32_t *)ctx->pos.p, cnt + 0, (const uint2 *)st.rects.p, (int)N,
+                    (uint32_t *)st.inst_a_t.p, (uint32_t *)st.inst_a_v.p, st.m_cap, VN, (uint32_t *)ctx->status.p, s);
+        launch_clamp_count(cnt + 1, st.m_cap, cnt + 2, s);
+    }
+    {
+        Phase ph(ctx, LVIGS_PHASE_TILE_SORT, s);
+        st.sorted_in_b = launch_radix_sort((uint32_t *)st.inst_a_t.p, (uint32_t *)st.inst_a_v.p,
+                                           (uint32_t *)st.inst_b_t.p, (uint32_t *)st.inst_b_v.p, cnt + 2, st.m_cap,
+                                           key_bits(st.vs.total_tiles), (uint32_t *)ctx->radix_tmp.p, s);
+    }
+    {
+        Phase ph(ctx, LVIGS_PHASE_RANGES, s);
+        launch_ranges(st.sorted_tiles(), cnt + 2, st.m_cap, (uint2 *)st.ranges.p, st.vs.total_tiles, s);
+    }
+    return LVIGS_OK;
+}
+
+lvigs_status upload_viewset(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
+    LV_TRY(ensure(ctx, st.vs_dev, sizeof(ViewSet)));
+    // the pinned staging copy is reused once the previous upload has landed
+    LV_CUDA(cudaEventSynchronize(ctx->vs_event));
+    std::memcpy(ctx->vs_staging, &st.vs, sizeof(ViewSet));
+    LV_CUDA(cudaMemcpyAsync(st.vs_dev.p, ctx->vs_staging, sizeof(ViewSet), cudaMemcpyHostToDevice, s));
+    LV_CUDA(cudaEventRecord(ctx->vs_event, s));
+    return LVIGS_OK;
+}
+
+int slot_index(const lvigs_ctx *ctx, int handle, RenderState **out) {
+    const int idx = handle & 0xfff;
+    const uint32_t gen = (uint32_t)handle >> 12;
+    if (handle < 0 || idx >= (int)ctx->slots.size()) return -1;
+    RenderState *s = ctx->slots[idx];
+    if (!s->valid || (s->generation & 0x7ffff) != gen) return -1;
+    *out = s;
+    return idx;
+}
+
+} // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *lvigs_version(void) { return "lvigs-gb300 0.1 (sm_103a)"; }
+
+void lvigs_config_default(lvigs_config *cfg) {
+    if (!cfg) return;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->batch_depth = 0;
+    cfg->max_workspace_bytes = 0;
+}
+
+lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
+    if (!out) return LVIGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    lvigs_config c;
+    lvigs_config_default(&c);
+    if (cfg) c = *cfg;
+    if (!tile_supported(c.tile_w, c.tile_h)) return LVIGS_ERR_INVALID_ARG;
+    if (c.batch_depth != 0 && c.batch_depth != c.tile_w * c.tile_h) return LVIGS_ERR_INVALID_ARG;
+    lvigs_ctx *ctx = new lvigs_ctx();
+    ctx->cfg = c;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_counters, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_losses, kMaxViews * 4 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_batch_counters, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->vs_staging, sizeof(ViewSet));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->vs_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->step_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lvigs_destroy(ctx);
+        return LVIGS_ERR_CUDA;
+    }
+    if (ensure(ctx, ctx->status, 16) != LVIGS_OK) {
+        lvigs_destroy(ctx);
+        return LVIGS_ERR_OUT_OF_MEMORY;
+    }
+    cudaMemset(ctx->status.p, 0, 16);
+    *out = ctx;
+    return LVIGS_OK;
+}
+
+void lvigs_destroy(lvigs_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    for (RenderState *s : ctx->slots) {
+        release_state(ctx, *s);
+        delete s;
+    }
+    release_state(ctx, ctx->batch);
+    DevBuf *shared[] = {&ctx->pos, &ctx->ck, &ctx->cv, &ctx->ck2, &ctx->cv2, &ctx->scan_tmp, &ctx->radix_tmp,
+                        &ctx->status, &ctx->g2d, &ctx->loss_tmp, &ctx->stats, &ctx->img_rgb, &ctx->img_depth,
+                        &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->losses_dev};
+    for (DevBuf *b : shared) release(ctx, *b);
+    for (int v = 0; v < kMaxViews; ++v) {
+        release(ctx, ctx->gt_stage[v]);
+        release(ctx, ctx->lidar_stage[v]);
+        for (int l = 0; l <= LVIGS_MAX_LEVEL; ++l) {
+            release(ctx, ctx->pyr_rgb[v][l]);
+            release(ctx, ctx->pyr_depth[v][l]);
+        }
+    }
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (auto &pe : ctx->prof_pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->vs_event) cudaEventDestroy(ctx->vs_event);
+    if (ctx->step_event) cudaEventDestroy(ctx->step_event);
+    if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
+    if (ctx->host_status) cudaFreeHost(ctx->host_status);
+    if (ctx->host_losses) cudaFreeHost(ctx->host_losses);
+    if (ctx->host_batch_counters) cudaFreeHost(ctx->host_batch_counters);
+    if (ctx->vs_staging) cudaFreeHost(ctx->vs_staging);
+    delete ctx;
+}
+
+lvigs_status lvigs_level_size(const lvigs_camera *cam, int level, int *width, int *height) {
+    if (!cam || !width || !height || level < 0 || level > LVIGS_MAX_LEVEL) return LVIGS_ERR_INVALID_ARG;
+    *width = cam->width >> level;
+    *height = cam->height >> level;
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam, int level,
+                          const lvigs_image_out *out, int *view_slot, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    LV_TRY(check_gauss(ctx, g));
+    LV_TRY(check_camera(ctx, cam, level));
+    if (!out || !out->rgb || !out->depth || !out->alpha || !view_slot)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    // pick a free slot
+    int idx = -1;
+    for (size_t i = 0; i < ctx->slots.size(); ++i)
+        if (!ctx->slots[i]->valid) {
+            idx = (int)i;
+            break;
+        }
+    if (idx < 0) {
+        if (ctx->slots.size() >= 4096) return fail(ctx, LVIGS_ERR_CAPACITY, "too many live view slots");
+        ctx->slots.push_back(new RenderState());
+        idx = (int)ctx->slots.size() - 1;
+    }
+    RenderState &st = *ctx->slots[idx];
+    st.P = to_params(g);
+    std::memset(&st.vs, 0, sizeof(ViewSet));
+    st.vs.n_views = 1;
+    st.vs.tile_w = ctx->cfg.tile_w;
+    st.vs.tile_h = ctx->cfg.tile_h;
+    st.vs.v[0] = make_view(*cam, level, ctx->cfg.tile_w, ctx->cfg.tile_h);
+    st.vs.v[0].tile_base = 0;
+    st.vs.v[0].pix_base = 0;
+    st.vs.total_tiles = (uint32_t)(st.vs.v[0].tiles_x * st.vs.v[0].tiles_y);
+    st.vs.total_pixels = (uint32_t)(st.vs.v[0].W * st.vs.v[0].H);
+    LV_TRY(upload_viewset(ctx, st, s));
+    LV_TRY(ensure(ctx, st.final_T, (size_t)st.vs.total_pixels * 4));
+    LV_TRY(ensure(ctx, st.n_contrib, (size_t)st.vs.total_pixels * 4));
+    LV_TRY(build_lists(ctx, st, s, true, 1.0));
+    ViewImages im{};
+    im.rgb[0] = out->rgb;
+    im.depth[0] = out->depth;
+    im.alpha[0] = out->alpha;
+    {
+        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
+        launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
+                             (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s);
+    }
+    LV_CUDA(cudaGetLastError());
+    st.valid = true;
+    st.generation = (st.generation + 1) & 0x7ffff;
+    *view_slot = (int)((st.generation << 12) | (uint32_t)idx);
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb, const float *dL_ddepth,
+                            const float *dL_dalpha, const lvigs_grads *grads, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    RenderState *st = nullptr;
+    if (slot_index(ctx, view_slot, &st) < 0) return fail(ctx, LVIGS_ERR_STATE, "stale or unknown view slot");
+    if (!grads || (st->P.n > 0 && (!grads->d_means || !grads->d_log_scales || !grads->d_quats ||
+                                   !grads->d_opacity_logits || !grads->d_sh)))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL gradient output");
+    if (!dL_drgb) return fail(ctx, LVIGS_ERR_INVALID_ARG, "dL_drgb is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t VN = (int64_t)st->P.n * st->vs.n_views;
+    LV_TRY(ensure(ctx, ctx->g2d, (size_t)VN * sizeof(GGrad)));
+    if (VN > 0) LV_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, (size_t)VN * sizeof(GGrad), s));
+    ViewGrads vg{};
+    vg.d_rgb[0] = dL_drgb;
+    vg.d_depth[0] = dL_ddepth;
+    vg.d_alpha[0] = dL_dalpha;
+    {
+        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
+        launch_composite_bwd(st->vs, (const ViewSet *)st->vs_dev.p, (const uint2 *)st->ranges.p, st->sorted_vals(),
+                             (const GRec *)st->recs.p, vg, (const float *)st->final_T.p,
+                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, s);
+    }
+    ParamGrads G{grads->d_means, grads->d_log_scales, grads->d_quats, grads->d_opacity_logits, grads->d_sh,
+                 grads->accumulate};
+    {
+        Phase ph(ctx, LVIGS_PHASE_PREPROCESS_BWD, s);
+        launch_preprocess_bwd(st->P, (const ViewSet *)st->vs_dev.p, (const uint32_t *)st->tiles.p,
+                              (const GGrad *)ctx->g2d.p, G, s);
+    }
+    LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb, const float *depth,
+                        const float *gt_rgb, const float *lidar_depth, float lambda_ssim, float lambda_depth,
+                        double *loss_out, float *d_rgb, float *d_depth, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    if (width <= 0 || height <= 0 || !rgb || !gt_rgb || !loss_out)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad loss arguments");
+    if (lidar_depth && !depth) return fail(ctx, LVIGS_ERR_INVALID_ARG, "lidar_depth given without depth");
+    if (!(lambda_ssim >= 0.f && lambda_ssim <= 1.f)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "lambda_ssim outside [0,1]");
+    LossViews lv{};
+    lv.n_views = 1;
+    lv.W[0] = width;
+    lv.H[0] = height;
+    lv.tile_base[0] = 0;
+    lv.total_tiles = (uint32_t)(((width + 15) / 16) * ((height + 15) / 16));
+    lv.rgb[0] = rgb;
+    lv.depth[0] = depth;
+    lv.gt[0] = gt_rgb;
+    lv.lidar[0] = lidar_depth;
+    lv.d_rgb[0] = d_rgb;
+    lv.d_depth[0] = d_depth;
+    lv.loss_out[0] = loss_out;
+    lv.lambda_ssim = lambda_ssim;
+    lv.lambda_depth = lambda_depth;
+    LV_TRY(ensure(ctx, ctx->loss_tmp, loss_tmp_bytes(lv)));
+    {
+        Phase ph(ctx, LVIGS_PHASE_LOSS, (cudaStream_t)stream);
+        launch_loss(lv, ctx->loss_tmp.p, (cudaStream_t)stream);
+    }
+    LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_pyramid_down(int width, int height, const float *rgb, const float *depth, float *rgb_out,
+                                float *depth_out, void *stream) {
+    if (width < 2 || height < 2 || !rgb || !rgb_out || (depth && !depth_out)) return LVIGS_ERR_INVALID_ARG;
+    launch_pyramid_down(width, height, rgb, depth, rgb_out, depth_out, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? LVIGS_OK : LVIGS_ERR_CUDA;
+}
+
+lvigs_status lvigs_debug_keys(lvigs_ctx *ctx, int view_slot, uint64_t *keys, uint32_t *vals, int64_t m_cap,
+                              int64_t *m, void *stream) {
+    if (!ctx || !m) return LVIGS_ERR_INVALID_ARG;
+    RenderState *st = nullptr;
+    if (slot_index(ctx, view_slot, &st) < 0) return fail(ctx, LVIGS_ERR_STATE, "stale or unknown view slot");
+    *m = st->m;
+    if (!keys) return LVIGS_OK;
+    if (!vals || m_cap < st->m) return fail(ctx, LVIGS_ERR_INVALID_ARG, "key buffer too small");
+    launch_debug_keys(st->sorted_tiles(), st->sorted_vals(), (const uint32_t *)st->zbits.p, st->P.n, keys, vals,
+                      st->m, (cudaStream_t)stream);
+    LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_debug_state(lvigs_ctx *ctx, int view_slot, uint32_t *ranges, int32_t *n_contrib,
+                               float *final_T, int *n_tiles, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    RenderState *st = nullptr;
+    if (slot_index(ctx, view_slot, &st) < 0) return fail(ctx, LVIGS_ERR_STATE, "stale or unknown view slot");
+    if (n_tiles) *n_tiles = (int)st->vs.total_tiles;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ranges)
+        LV_CUDA(cudaMemcpyAsync(ranges, st->ranges.p, sizeof(uint2) * st->vs.total_tiles, cudaMemcpyDeviceToDevice, s));
+    if (n_contrib)
+        LV_CUDA(cudaMemcpyAsync(n_contrib, st->n_contrib.p, 4 * (size_t)st->vs.total_pixels, cudaMemcpyDeviceToDevice, s));
+    if (final_T)
+        LV_CUDA(cudaMemcpyAsync(final_T, st->final_T.p, 4 * (size_t)st->vs.total_pixels, cudaMemcpyDeviceToDevice, s));
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_sync_status(lvigs_ctx *ctx, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    LV_CUDA(cudaMemcpyAsync(ctx->host_status, ctx->status.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const uint32_t st = *ctx->host_status;
+    if (st) LV_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(uint32_t), s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    if (st & kStatusTimeout) return fail(ctx, LVIGS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & kStatusCapacity) return fail(ctx, LVIGS_ERR_CAPACITY, "instance capacity exceeded on the device");
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_release_view(lvigs_ctx *ctx, int view_slot) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    RenderState *st = nullptr;
+    if (slot_index(ctx, view_slot, &st) < 0) return fail(ctx, LVIGS_ERR_STATE, "stale or unknown view slot");
+    st->valid = false;
+    return LVIGS_OK;
+}
+
+const char *lvigs_last_error(const lvigs_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+lvigs_status lvigs_step_stats(lvigs_ctx *ctx, int64_t *out, void *stream) {
+    if (!ctx || !out) return LVIGS_ERR_INVALID_ARG;
+    RenderState &st = ctx->batch;
+    cudaStream_t s = (cudaStream_t)stream;
+    out[0] = out[1] = out[2] = out[3] = 0;
+    if (!st.counters.p || !st.n_contrib.p) return LVIGS_OK;
+    LV_TRY(ensure(ctx, ctx->stats, 16));
+    launch_sum_i32((const int32_t *)st.n_contrib.p, st.vs.total_pixels, (unsigned long long *)ctx->stats.p, s);
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, st.counters.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    unsigned long long sum = 0;
+    LV_CUDA(cudaMemcpyAsync(&sum, ctx->stats.p, sizeof(sum), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    out[0] = ctx->host_counters[0];
+    out[1] = ctx->host_counters[1];
+    out[2] = (int64_t)sum;
+    out[3] = st.vs.total_pixels;
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_profile_enable(lvigs_ctx *ctx, int enable) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    ctx->prof = enable != 0;
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_profile_read(lvigs_ctx *ctx, double *ms, int64_t *calls, int *kernels_per_step) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    for (auto &pe : ctx->prof_pending) {
+        cudaEvent_t e0 = pe.second.first, e1 = pe.second.second;
+        float t = 0.f;
+        LV_CUDA(cudaEventSynchronize(e1));
+        LV_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        ctx->prof_ms[pe.first] += t;
+        ctx->prof_calls[pe.first] += 1;
+        ctx->ev_pool.push_back(e0);
+        ctx->ev_pool.push_back(e1);
+    }
+    ctx->prof_pending.clear();
+    for (int i = 0; i < LVIGS_N_PHASES; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (calls) calls[i] = ctx->prof_calls[i];
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_calls[i] = 0;
+    }
+    if (kernels_per_step) *kernels_per_step = ctx->kernels_per_step;
+    return LVIGS_OK;
+}
+
+} // extern "C"
+
+// ===========================================================================
+// Batched step
+// ===========================================================================
+namespace {
+
+// Everything of one batched step, enqueued on `s`.  eager: may allocate and
+// waits once to size the instance list; otherwise no allocation and no wait
+// (capture-safe).
+lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *b, const lvigs_grads *gr,
+                          cudaStream_t s, bool eager) {
+    RenderState &st = ctx->batch;
+    const int V = b->n_views;
+    const bool host_tg = (b->flags & LVIGS_STEP_HOST_TARGETS) != 0;
+    // 1. targets at each view's level (Sec. III-D)
+    const float *gt_l[kMaxViews];
+    const float *li_l[kMaxViews];
+    for (int v = 0; v < V; ++v) {
+        const lvigs_camera &c = b->cameras[v];
+        const size_t P0 = (size_t)c.width * c.height;
+        const float *gsrc = b->gt_rgb[v];
+        const float *lsrc = b->lidar_depth ? b->lidar_depth[v] : nullptr;
+        if (host_tg) {
+            LV_TRY(ensure(ctx, ctx->gt_stage[v], 3 * P0 * 4));
+            LV_CUDA(cudaMemcpyAsync(ctx->gt_stage[v].p, gsrc, 3 * P0 * 4, cudaMemcpyHostToDevice, s));
+            gsrc = (const float *)ctx->gt_stage[v].p;
+            if (lsrc) {
+                LV_TRY(ensure(ctx, ctx->lidar_stage[v], P0 * 4));
+                LV_CUDA(cudaMemcpyAsync(ctx->lidar_stage[v].p, lsrc, P0 * 4, cudaMemcpyHostToDevice, s));
+                lsrc = (const float *)ctx->lidar_stage[v].p;
+            }
+        }
+        int W = c.width, H = c.height;
+        Phase ph(ctx, LVIGS_PHASE_PYRAMID, s);
+        for (int l = 1; l <= b->levels[v]; ++l) {
+            const int W2 = W / 2, H2 = H / 2;
+            LV_TRY(ensure(ctx, ctx->pyr_rgb[v][l], 3 * (size_t)W2 * H2 * 4));
+            if (lsrc) LV_TRY(ensure(ctx, ctx->pyr_depth[v][l], (size_t)W2 * H2 * 4));
+            launch_pyramid_down(W, H, gsrc, lsrc, (float *)ctx->pyr_rgb[v][l].p,
+                                lsrc ? (float *)ctx->pyr_depth[v][l].p : nullptr, s);
+            gsrc = (const float *)ctx->pyr_rgb[v][l].p;
+            if (lsrc) lsrc = (const float *)ctx->pyr_depth[v][l].p;
+            W = W2;
+            H = H2;
+        }
+        gt_l[v] = gsrc;
+        li_l[v] = lsrc;
+    }
+    // 2. a1-a4 over all views at once
+    LV_TRY(build_lists(ctx, st, s, eager, 1.3));
+    // 3. a5 into the caller's images or the internal ones
+    const size_t TP = st.vs.total_pixels;
+    LV_TRY(ensure(ctx, st.final_T, TP * 4));
+    LV_TRY(ensure(ctx, st.n_contrib, TP * 4));
+    LV_TRY(ensure(ctx, ctx->img_rgb, 3 * TP * 4));
+    LV_TRY(ensure(ctx, ctx->img_depth, TP * 4));
+    LV_TRY(ensure(ctx, ctx->img_alpha, TP * 4));
+    LV_TRY(ensure(ctx, ctx->d_rgb, 3 * TP * 4));
+    LV_TRY(ensure(ctx, ctx->d_depth, TP * 4));
+    LV_TRY(ensure(ctx, ctx->losses_dev, kMaxViews * 4 * sizeof(double)));
+    ViewImages im{};
+    ViewGrads vg{};
+    LossViews lv{};
+    lv.n_views = V;
+    uint32_t ltiles = 0;
+    for (int v = 0; v < V; ++v) {
+        const ViewDesc &d = st.vs.v[v];
+        const size_t pb = d.pix_base;
+        im.rgb[v] = b->rgb_out && b->rgb_out[v] ? b->rgb_out[v] : (float *)ctx->img_rgb.p + 3 * pb;
+        im.depth[v] = b->depth_out && b->depth_out[v] ? b->depth_out[v] : (float *)ctx->img_depth.p + pb;
+        im.alpha[v] = b->alpha_out && b->alpha_out[v] ? b->alpha_out[v] : (float *)ctx->img_alpha.p + pb;
+        vg.d_rgb[v] = (float *)ctx->d_rgb.p + 3 * pb;
+        vg.d_depth[v] = (float *)ctx->d_depth.p + pb;
+        vg.d_alpha[v] = nullptr;
+        lv.W[v] = d.W;
+        lv.H[v] = d.H;
+        lv.tile_base[v] = ltiles;
+        ltiles += (uint32_t)(((d.W + 15) / 16) * ((d.H + 15) / 16));
+        lv.rgb[v] = im.rgb[v];
+        lv.depth[v] = im.depth[v];
+        lv.gt[v] = gt_l[v];
+        lv.lidar[v] = li_l[v];
+        lv.d_rgb[v] = (float *)vg.d_rgb[v];
+        lv.d_depth[v] = (float *)vg.d_depth[v];
+        lv.loss_out[v] = (double *)ctx->losses_dev.p + 4 * v;
+    }
+    lv.total_tiles = ltiles;
+    lv.lambda_ssim = b->lambda_ssim;
+    lv.lambda_depth = b->lambda_depth;
+    LV_TRY(ensure(ctx, ctx->loss_tmp, loss_tmp_bytes(lv)));
+    const ViewSet *vsd = (const ViewSet *)st.vs_dev.p;
+    {
+        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
+        launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
+                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s);
+    }
+    // 4. a8: loss and its image gradients for every view
+    {
+        Phase ph(ctx, LVIGS_PHASE_LOSS, s);
+        launch_loss(lv, ctx->loss_tmp.p, s);
+    }
+    if (b->flags & LVIGS_STEP_HOST_LOSS)
+        LV_CUDA(cudaMemcpyAsync(ctx->host_losses, ctx->losses_dev.p, (size_t)V * 4 * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    else
+        LV_CUDA(cudaMemcpyAsync(b->losses, ctx->losses_dev.p, (size_t)V * 4 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+    // 5. a6 + a7
+    const int64_t VN = (int64_t)st.P.n * V;
+    LV_TRY(ensure(ctx, ctx->g2d, (size_t)VN * sizeof(GGrad)));
+    if (VN > 0) LV_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, (size_t)VN * sizeof(GGrad), s));
+    {
+        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
+        launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
+                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, s);
+    }
+    ParamGrads G{gr->d_means, gr->d_log_scales, gr->d_quats, gr->d_opacity_logits, gr->d_sh, gr->accumulate};
+    {
+        Phase ph(ctx, LVIGS_PHASE_PREPROCESS_BWD, s);
+        launch_preprocess_bwd(st.P, vsd, (const uint32_t *)st.tiles.p, (const GGrad *)ctx->g2d.p, G, s);
+    }
+    // instance count of this step, for the capacity check of the next one
+    LV_CUDA(cudaMemcpyAsync(ctx->host_batch_counters, st.counters.p, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    return LVIGS_OK;
+}
+
+BatchKey make_key(const lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *b, const lvigs_grads *gr) {
+    BatchKey k;
+    auto add = [&](uint64_t x) { k.k.push_back(x); };
+    auto addp = [&](const void *p) { k.k.push_back((uint64_t)(uintptr_t)p); };
+    auto addf = [&](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        k.k.push_back(u);
+    };
+    add(ctx->ws_epoch);
+    add((uint64_t)ctx->batch.m_cap);
+    add((uint64_t)g->n);
+    add((uint64_t)g->sh_degree);
+    add((uint64_t)g->sh_stride_k);
+    addp(g->means);
+    addp(g->log_scales);
+    addp(g->quats);
+    addp(g->opacity_logits);
+    addp(g->sh);
+    addp(gr->d_means);
+    addp(gr->d_log_scales);
+    addp(gr->d_quats);
+    addp(gr->d_opacity_logits);
+    addp(gr->d_sh);
+    add((uint64_t)gr->accumulate);
+    add((uint64_t)b->n_views);
+    add((uint64_t)b->flags);
+    addf(b->lambda_ssim);
+    addf(b->lambda_depth);
+    addp(b->losses);
+    for (int v = 0; v < b->n_views; ++v) {
+        add((uint64_t)b->cameras[v].width);
+        add((uint64_t)b->cameras[v].height);
+        add((uint64_t)b->levels[v]);
+        addp(b->gt_rgb[v]);
+        addp(b->lidar_depth ? b->lidar_depth[v] : nullptr);
+        addp(b->rgb_out ? b->rgb_out[v] : nullptr);
+        addp(b->depth_out ? b->depth_out[v] : nullptr);
+        addp(b->alpha_out ? b->alpha_out[v] : nullptr);
+    }
+    return k;
+}
+
+} // namespace
+
+extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *b,
+                                                 const lvigs_grads *gr, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    LV_TRY(check_gauss(ctx, g));
+    if (!b || b->n_views < 1 || b->n_views > kMaxViews || !b->cameras || !b->levels || !b->gt_rgb || !b->losses)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad batch description");
+    if (!gr || (g->n > 0 && (!gr->d_means || !gr->d_log_scales || !gr->d_quats || !gr->d_opacity_logits ||
+                             !gr->d_sh)))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL gradient output");
+    if (!(b->lambda_ssim >= 0.f && b->lambda_ssim <= 1.f))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "lambda_ssim outside [0,1]");
+    if ((uint64_t)g->n * (uint64_t)b->n_views >= 0xffffffffull)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "n * n_views must be below 2^32");
+    for (int v = 0; v < b->n_views; ++v) {
+        LV_TRY(check_camera(ctx, &b->cameras[v], b->levels[v]));
+        if (!b->gt_rgb[v]) return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL target image");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    RenderState &st = ctx->batch;
+    // view set (cameras may change every step without a new graph)
+    std::memset(&st.vs, 0, sizeof(ViewSet));
+    st.vs.n_views = b->n_views;
+    st.vs.tile_w = ctx->cfg.tile_w;
+    st.vs.tile_h = ctx->cfg.tile_h;
+    uint32_t tb = 0, pb = 0;
+    for (int v = 0; v < b->n_views; ++v) {
+        ViewDesc d = make_view(b->cameras[v], b->levels[v], ctx->cfg.tile_w, ctx->cfg.tile_h);
+        d.tile_base = tb;
+        d.pix_base = pb;
+        tb += (uint32_t)(d.tiles_x * d.tiles_y);
+        pb += (uint32_t)(d.W * d.H);
+        st.vs.v[v] = d;
+    }
+    st.vs.total_tiles = tb;
+    st.vs.total_pixels = pb;
+    st.P = to_params(g);
+    LV_TRY(upload_viewset(ctx, st, s));
+
+    // capacity check of the previous step (non-blocking unless it has finished)
+    bool grow = false;
+    if (ctx->step_pending && cudaEventQuery(ctx->step_event) == cudaSuccess) {
+        ctx->step_pending = false;
+        if ((int64_t)ctx->host_batch_counters[1] > st.m_cap) grow = true;
+    }
+    cudaGetLastError();
+
+    const bool use_graph = !(b->flags & LVIGS_STEP_NO_GRAPH);
+    BatchKey key = make_key(ctx, g, b, gr);
+    if (!use_graph || grow || st.m_cap == 0) {
+        // eager step: sizes the instance capacity (waits once on the stream)
+        LV_TRY(batched_body(ctx, g, b, gr, s, true));
+    } else {
+        if (!ctx->graph_ok || !(key == ctx->graph_key)) {
+            if (ctx->graph_exec) {
+                cudaGraphExecDestroy(ctx->graph_exec);
+                ctx->graph_exec = nullptr;
+            }
+            ctx->graph_ok = false;
+            // the capture stream waits for nothing; the graph is launched on `s`
+            ctx->capturing = true;
+            ctx->capture_short = false;
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            lvigs_status bs = LVIGS_OK;
+            if (e == cudaSuccess) bs = batched_body(ctx, g, b, gr, ctx->cap_stream, false);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            ctx->capturing = false;
+            if (e == cudaSuccess && e2 == cudaSuccess && bs == LVIGS_OK && !ctx->capture_short) {
+                size_t nn = 0;
+                if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+                    std::vector<cudaGraphNode_t> nodes(nn);
+                    cudaGraphGetNodes(graph, nodes.data(), &nn);
+                    int kc = 0;
+                    for (auto nd : nodes) {
+                        cudaGraphNodeType ty;
+                        if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kc;
+                    }
+                    ctx->kernels_per_step = kc;
+                }
+                e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+                if (e == cudaSuccess) {
+                    ctx->graph_ok = true;
+                    ctx->graph_key = key;
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+        }
+        if (ctx->graph_ok) {
+            LV_CUDA(cudaGraphLaunch(ctx->graph_exec, s));
+        } else {
+            LV_TRY(batched_body(ctx, g, b, gr, s, true));
+        }
+    }
+    LV_CUDA(cudaEventRecord(ctx->step_event, s));
+    ctx->step_pending = true;
+    if (b->flags & LVIGS_STEP_HOST_LOSS) {
+        LV_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(b->losses, ctx->host_losses, (size_t)b->n_views * 4 * sizeof(double));
+    }
+    LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}

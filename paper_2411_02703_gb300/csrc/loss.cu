@@ -1,0 +1,346 @@
+// loss.cu -- fused mapping loss (a8) and image pyramid (a9).
+//
+// L = (1 - lambda) L1 + lambda (1 - mean SSIM) + lambda_d L_d   (Eq. 10-12)
+//
+// Pass 1, one CTA per 16x16 pixel tile (of every view of the call): stages
+// the rendered and target images of the tile plus a 5-pixel halo in shared
+// memory, forms the five windowed moments of each channel with a separable
+// 11-tap Gaussian (sigma 1.5, zero padding), and writes per pixel the three
+// partial derivatives of SSIM with respect to the moments (mu_x, E[x^2],
+// E[xy]); it also reduces the L1, SSIM and LiDAR-depth sums of the tile.
+// A one-block-per-view kernel sums the tile partials in a fixed order
+// (deterministic) into the four loss terms.
+// Pass 2 applies the adjoint window to those derivative maps and adds the
+// L1 and depth terms, giving dL/drgb and dL/ddepth.
+#include <cmath>
+
+#include "lvigs_internal.cuh"
+
+namespace lvigs {
+namespace {
+
+constexpr int LT = 16;          // loss tile
+constexpr int HALO = 5;         // (11 - 1) / 2
+constexpr int LS = LT + 2 * HALO; // 26
+
+struct Window {
+    float w[11];
+};
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+__device__ __forceinline__ void loss_tile_of(const LossViews &lv, uint32_t b, int &vi, int &tx, int &ty) {
+    vi = 0;
+    for (int i = 1; i < lv.n_views; ++i)
+        if (lv.tile_base[i] <= b) vi = i;
+    const uint32_t lt = b - lv.tile_base[vi];
+    const int tiles_x = (lv.W[vi] + LT - 1) / LT;
+    tx = (int)(lt % (uint32_t)tiles_x);
+    ty = (int)(lt / (uint32_t)tiles_x);
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+    // 256 threads
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w) s += red[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(256)
+loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *__restrict__ partials) {
+    __shared__ float sx[LS][LS], sy[LS][LS];
+    __shared__ float sh[5][LS][LT];
+    __shared__ double red[8];
+    int vi, tx, ty;
+    loss_tile_of(lv, blockIdx.x, vi, tx, ty);
+    const int W = lv.W[vi], H = lv.H[vi];
+    const size_t HW = (size_t)W * H;
+    const int t = threadIdx.x;
+    const int lx = t % LT, ly = t / LT;
+    const int px = tx * LT + lx, py = ty * LT + ly;
+    const bool inside = px < W && py < H;
+    const size_t p = (size_t)py * W + px;
+    const float lam = lv.lambda_ssim;
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    double l1 = 0.0, ssim = 0.0, dsum = 0.0, dcnt = 0.0;
+    float *G = gmaps + lv.gmap_base[vi];
+
+    for (int ch = 0; ch < 3; ++ch) {
+        const float *x = lv.rgb[vi] + ch * HW;
+        const float *y = lv.gt[vi] + ch * HW;
+        if (inside) l1 += fabsf(x[p] - y[p]);
+        if (lam == 0.f) continue;
+        __syncthreads();
+        for (int i = t; i < LS * LS; i += 256) {
+            const int r = i / LS, c = i % LS;
+            const int gx = tx * LT + c - HALO, gy = ty * LT + r - HALO;
+            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            sx[r][c] = ok ? x[(size_t)gy * W + gx] : 0.f;
+            sy[r][c] = ok ? y[(size_t)gy * W + gx] : 0.f;
+        }
+        __syncthreads();
+        // horizontal pass over all LS rows, LT columns
+        for (int i = t; i < LS * LT; i += 256) {
+            const int r = i / LT, c = i % LT;
+            float m1 = 0.f, m2 = 0.f, m11 = 0.f, m22 = 0.f, m12 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                const float a = sx[r][c + k], b = sy[r][c + k], w = win.w[k];
+                m1 = fmaf(w, a, m1);
+                m2 = fmaf(w, b, m2);
+                m11 = fmaf(w, a * a, m11);
+                m22 = fmaf(w, b * b, m22);
+                m12 = fmaf(w, a * b, m12);
+            }
+            sh[0][r][c] = m1;
+            sh[1][r][c] = m2;
+            sh[2][r][c] = m11;
+            sh[3][r][c] = m22;
+            sh[4][r][c] = m12;
+        }
+        __syncthreads();
+        float mx = 0.f, my = 0.f, mxx = 0.f, myy = 0.f, mxy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = win.w[k];
+            mx = fmaf(w, sh[0][ly + k][lx], mx);
+            my = fmaf(w, sh[1][ly + k][lx], my);
+            mxx = fmaf(w, sh[2][ly + k][lx], mxx);
+            myy = fmaf(w, sh[3][ly + k][lx], myy);
+            mxy = fmaf(w, sh[4][ly + k][lx], mxy);
+        }
+        if (inside) {
+            const float vx = mxx - mx * mx, vy = myy - my * my, cxy = mxy - mx * my;
+            const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
+            const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
+            const float inv = 1.f / (B1 * B2);
+            const float S = A1 * A2 * inv;
+            ssim += S;
+            // dS/d mu_x, dS/d E[x^2], dS/d E[xy]
+            const float d1 = 2.f * my * (A2 - A1) * inv - S * (2.f * mx / B1 - 2.f * mx / B2);
+            const float d2 = -S / B2;
+            const float d12 = 2.f * A1 * inv;
+            G[(0 * 3 + ch) * HW + p] = d1;
+            G[(1 * 3 + ch) * HW + p] = d2;
+            G[(2 * 3 + ch) * HW + p] = d12;
+        }
+    }
+    if (inside && lv.lidar[vi]) {
+        const float L = lv.lidar[vi][p];
+        if (L > 0.f) {
+            dsum = fabsf(lv.depth[vi][p] - L);
+            dcnt = 1.0;
+        }
+    }
+    const double s0 = block_sum_d(l1, red);
+    const double s1 = block_sum_d(ssim, red);
+    const double s2 = block_sum_d(dsum, red);
+    const double s3 = block_sum_d(dcnt, red);
+    if (t == 0) {
+        double *o = partials + 4 * (size_t)blockIdx.x;
+        o[0] = s0;
+        o[1] = s1;
+        o[2] = s2;
+        o[3] = s3;
+    }
+}
+
+// One block per view: fixed-order sum of the tile partials.
+__global__ void __launch_bounds__(256)
+loss_reduce_kernel(LossViews lv, const double *__restrict__ partials, double *__restrict__ nvalid_out) {
+    __shared__ double red[4][256];
+    const int vi = blockIdx.x;
+    const uint32_t b0 = lv.tile_base[vi];
+    const uint32_t b1 = vi + 1 < lv.n_views ? lv.tile_base[vi + 1] : lv.total_tiles;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint32_t b = b0 + threadIdx.x; b < b1; b += 256)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] += partials[4 * (size_t)b + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int stride = 128; stride > 0; stride >>= 1) {
+        if (threadIdx.x < stride)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double P3 = 3.0 * lv.W[vi] * lv.H[vi];
+        const double lam = lv.lambda_ssim, lamd = lv.lambda_depth;
+        const double l1 = red[0][0] / P3;
+        const double ssim = lam != 0.0 ? red[1][0] / P3 : 1.0;
+        const double nv = red[3][0];
+        const double ld = nv > 0 ? red[2][0] / nv : 0.0;
+        double *o = lv.loss_out[vi];
+        if (o) {
+            o[0] = (1.0 - lam) * l1 + (lam != 0.0 ? lam * (1.0 - ssim) : 0.0) + lamd * ld;
+            o[1] = l1;
+            o[2] = ssim;
+            o[3] = ld;
+        }
+        nvalid_out[vi] = nv;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+loss_pass2_kernel(LossViews lv, Window win, const float *__restrict__ gmaps,
+                  const double *__restrict__ nvalid) {
+    __shared__ float sg[3][LS][LS];
+    __shared__ float sh[3][LS][LT];
+    int vi, tx, ty;
+    loss_tile_of(lv, blockIdx.x, vi, tx, ty);
+    const int W = lv.W[vi], H = lv.H[vi];
+    const size_t HW = (size_t)W * H;
+    const int t = threadIdx.x;
+    const int lx = t % LT, ly = t / LT;
+    const int px = tx * LT + lx, py = ty * LT + ly;
+    const bool inside = px < W && py < H;
+    const size_t p = (size_t)py * W + px;
+    const float lam = lv.lambda_ssim;
+    const float k1 = (1.f - lam) / (float)(3.0 * HW);
+    const float k2 = -lam / (float)(3.0 * HW);
+    const float *G = gmaps + lv.gmap_base[vi];
+    float *drgb = lv.d_rgb[vi];
+
+    for (int ch = 0; ch < 3; ++ch) {
+        const float *x = lv.rgb[vi] + ch * HW;
+        const float *y = lv.gt[vi] + ch * HW;
+        float s1 = 0.f, s2 = 0.f, s12 = 0.f;
+        if (lam != 0.f) {
+            __syncthreads();
+            for (int i = t; i < LS * LS; i += 256) {
+                const int r = i / LS, c = i % LS;
+                const int gx = tx * LT + c - HALO, gy = ty * LT + r - HALO;
+                const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+                const size_t q = (size_t)gy * W + gx;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) sg[m][r][c] = ok ? G[(m * 3 + ch) * HW + q] : 0.f;
+            }
+            __syncthreads();
+            for (int i = t; i < LS * LT; i += 256) {
+                const int r = i / LT, c = i % LT;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    const float w = win.w[k];
+                    a0 = fmaf(w, sg[0][r][c + k], a0);
+                    a1 = fmaf(w, sg[1][r][c + k], a1);
+                    a2 = fmaf(w, sg[2][r][c + k], a2);
+                }
+                sh[0][r][c] = a0;
+                sh[1][r][c] = a1;
+                sh[2][r][c] = a2;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 11; ++k) {
+                const float w = win.w[k];
+                s1 = fmaf(w, sh[0][ly + k][lx], s1);
+                s2 = fmaf(w, sh[1][ly + k][lx], s2);
+                s12 = fmaf(w, sh[2][ly + k][lx], s12);
+            }
+        }
+        if (inside && drgb) {
+            const float xv = x[p], yv = y[p];
+            drgb[ch * HW + p] = k1 * sgnf(xv - yv) + k2 * (s1 + 2.f * xv * s2 + yv * s12);
+        }
+    }
+    if (inside && lv.d_depth[vi]) {
+        float g = 0.f;
+        if (lv.lidar[vi]) {
+            const float L = lv.lidar[vi][p];
+            const double nv = nvalid[vi];
+            if (L > 0.f && nv > 0) g = lv.lambda_depth * sgnf(lv.depth[vi][p] - L) / (float)nv;
+        }
+        lv.d_depth[vi][p] = g;
+    }
+}
+
+__global__ void pyramid_down_kernel(int W, int H, const float *__restrict__ rgb,
+                                    const float *__restrict__ depth, float *__restrict__ rgb_out,
+                                    float *__restrict__ depth_out) {
+    const int W2 = W / 2, H2 = H / 2;
+    const int n = W2 * H2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = i % W2, y = i / W2;
+        const size_t q00 = (size_t)(2 * y) * W + 2 * x, q10 = q00 + W;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            const float *s = rgb + (size_t)ch * W * H;
+            rgb_out[(size_t)ch * n + i] = 0.25f * ((s[q00] + s[q00 + 1]) + (s[q10] + s[q10 + 1]));
+        }
+        if (depth) {
+            const float d[4] = {depth[q00], depth[q00 + 1], depth[q10], depth[q10 + 1]};
+            float sum = 0.f;
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (d[k] > 0.f) {
+                    sum += d[k];
+                    ++cnt;
+                }
+            depth_out[i] = cnt ? sum / (float)cnt : 0.f;
+        }
+    }
+}
+
+Window make_window() {
+    Window w;
+    double g[11], s = 0.0;
+    for (int i = 0; i < 11; ++i) {
+        g[i] = std::exp(-((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
+        s += g[i];
+    }
+    for (int i = 0; i < 11; ++i) w.w[i] = (float)(g[i] / s);
+    return w;
+}
+
+} // namespace
+
+// Workspace: derivative maps (9 floats per pixel), their per-view bases,
+// tile partials (4 doubles per tile), per-view valid counts.
+size_t loss_tmp_bytes(const LossViews &lv) {
+    size_t pix = 0;
+    for (int v = 0; v < lv.n_views; ++v) pix += (size_t)lv.W[v] * lv.H[v];
+    return pix * 9 * sizeof(float) + 256 + (size_t)lv.total_tiles * 4 * sizeof(double) +
+           kMaxViews * sizeof(double) + 256;
+}
+
+void launch_loss(const LossViews &lv_in, void *tmp, cudaStream_t s) {
+    if (lv_in.total_tiles == 0) return;
+    LossViews lv = lv_in;
+    size_t pix = 0;
+    for (int v = 0; v < lv.n_views; ++v) {
+        lv.gmap_base[v] = pix * 9;
+        pix += (size_t)lv.W[v] * lv.H[v];
+    }
+    char *base = (char *)tmp;
+    float *gmaps = (float *)base;
+    size_t off = (pix * 9 * sizeof(float) + 255) / 256 * 256;
+    double *partials = (double *)(base + off);
+    off += (size_t)lv.total_tiles * 4 * sizeof(double);
+    double *nvalid = (double *)(base + off);
+    const Window win = make_window();
+    loss_pass1_kernel<<<lv.total_tiles, 256, 0, s>>>(lv, win, gmaps, partials);
+    loss_reduce_kernel<<<lv.n_views, 256, 0, s>>>(lv, partials, nvalid);
+    loss_pass2_kernel<<<lv.total_tiles, 256, 0, s>>>(lv, win, gmaps, nvalid);
+}
+
+void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, float *rgb_out,
+                         float *depth_out, cudaStream_t s) {
+    const int n = (W / 2) * (H / 2);
+    if (n <= 0) return;
+    int blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    pyramid_down_kernel<<<blocks, 256, 0, s>>>(W, H, rgb, depth, rgb_out, depth_out);
+}
+
+} // namespace lvigs

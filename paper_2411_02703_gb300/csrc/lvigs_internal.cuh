@@ -1,0 +1,164 @@
+// lvigs_internal.cuh -- device-side structures shared by the kernels of the
+// GB300 Gaussian-splatting hot path.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lvigs {
+
+constexpr int kMaxViews = 32;
+
+// Status bits latched on the device and read back by lvigs_sync_status.
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+// One view at its pyramid level, as the kernels see it.
+struct ViewDesc {
+    float R[9];         // world -> camera rotation, row-major (Q_iw of Eq. 7)
+    float t[3];         // world -> camera translation (T_iw of Eq. 7)
+    float fx, fy, cx, cy;
+    float limx, limy;   // Jacobian clamp: 1.3 * tan(half field of view)
+    float campos[3];    // camera centre in world coordinates (SH view direction)
+    int W, H;
+    int tiles_x, tiles_y;
+    uint32_t tile_base; // first global tile id of this view
+    uint32_t pix_base;  // first pixel of this view in packed per-pixel buffers
+};
+
+struct ViewSet {
+    int n_views;
+    int tile_w, tile_h;
+    uint32_t total_tiles;
+    uint32_t total_pixels;
+    ViewDesc v[kMaxViews];
+};
+
+// Per-view image pointers (device).
+struct ViewImages {
+    float *rgb[kMaxViews];
+    float *depth[kMaxViews];
+    float *alpha[kMaxViews];
+};
+
+struct ViewGrads {
+    const float *d_rgb[kMaxViews];
+    const float *d_depth[kMaxViews];
+    const float *d_alpha[kMaxViews]; // may be null
+};
+
+// Gaussian parameters (device, SoA, caller-owned).
+struct GaussParams {
+    const float *means, *log_scales, *quats, *opacity_logits, *sh;
+    int n;
+    int sh_degree;
+    int sh_stride_k;
+};
+
+struct ParamGrads {
+    float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_sh;
+    int accumulate;
+};
+
+// Screen-space record of one (view, Gaussian), written by preprocessing and
+// gathered by the compositing kernels: a = (u, v, A, B), b = (C, opacity, z, -),
+// c = (r, g, b, -), with the conic [[A, B], [B, C]].
+struct __align__(16) GRec {
+    float4 a, b, c;
+};
+
+// Screen-space gradient of one (view, Gaussian): g0 = (du, dv, dA, dB),
+// g1 = (dC, dopacity, dz, -), g2 = (dr, dg, db, -).
+struct __align__(16) GGrad {
+    float4 g0, g1, g2;
+};
+
+__host__ __device__ inline int view_of_tile(const ViewSet &vs, uint32_t gt) {
+    int v = 0;
+#pragma unroll 1
+    for (int i = 1; i < vs.n_views; ++i)
+        if (vs.v[i].tile_base <= gt) v = i;
+    return v;
+}
+
+// Alpha of Eq. (6) at pixel offset (dx, dy) = (u - px, v - py).  Written with
+// explicit rounding so the forward and backward kernels take identical
+// branches on the 0.99 / (1/255) tests.
+__device__ __forceinline__ float gauss_power(float A, float B, float C, float dx, float dy) {
+    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, q, -__fmul_rn(B, __fmul_rn(dx, dy)));
+}
+
+} // namespace lvigs
+
+// Kernel launchers (defined in the .cu files, called from the host API).
+namespace lvigs {
+
+// ViewSet pointers passed to kernels are DEVICE copies; the host copy (by
+// reference) is only used to size grids.
+void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs_dev, GRec *recs, uint32_t *tiles,
+                           uint32_t *zbits, uint2 *rects, cudaStream_t s);
+void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs_dev, const uint32_t *tiles,
+                           const GGrad *g2d, const ParamGrads &G, cudaStream_t s);
+
+// Device-wide exclusive scan of n items (n read from the device when n_dev is
+// non-null, else n_host).  in[i] is gathered as in[gather[i]] when gather is
+// non-null; with flag_only the item is (in[i] != 0).  Writes out[i] and, at
+// out_total, the total.  tmp needs scan_tmp_words(n_host) uint32 words.
+size_t scan_tmp_words(int64_t n_max);
+void launch_scan(const uint32_t *in, const uint32_t *gather, int flag_only, uint32_t *out,
+                 uint32_t *out_total, const uint32_t *n_dev, int64_t n_max, uint32_t *tmp,
+                 cudaStream_t s);
+
+// Compaction of visible (tiles > 0) items: keys = zbits[i], vals = i.
+void launch_compact(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
+                    uint32_t *keys, uint32_t *vals, int64_t n, cudaStream_t s);
+
+// LSD radix sort of (key, value) pairs over bits [0, bits).  Stable.
+// n read from the device.  Returns 1 when the result ends in the alt buffers.
+size_t radix_tmp_words(int64_t n_max);
+int launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                       const uint32_t *n_dev, int64_t n_max, int bits, uint32_t *tmp,
+                       cudaStream_t s);
+
+void launch_emit(const ViewSet *vs_dev, const uint32_t *sorted_idx, const uint32_t *offsets,
+                 const uint32_t *n_vis_dev, const uint2 *rects, int n_gauss, uint32_t *tile_ids,
+                 uint32_t *inst_vals, int64_t m_cap, int64_t n_max, uint32_t *status,
+                 cudaStream_t s);
+void launch_ranges(const uint32_t *tile_ids, const uint32_t *m_dev, int64_t m_cap,
+                   uint2 *ranges, uint32_t total_tiles, cudaStream_t s);
+void launch_sum_i32(const int32_t *x, uint32_t n, unsigned long long *out, cudaStream_t s);
+void launch_clamp_count(const uint32_t *m_dev, int64_t m_cap, uint32_t *out, cudaStream_t s);
+void launch_debug_keys(const uint32_t *tile_ids, const uint32_t *inst_vals, const uint32_t *zbits,
+                       int n_gauss, uint64_t *keys, uint32_t *vals, int64_t m, cudaStream_t s);
+
+void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
+                          const GRec *recs, const ViewImages &out, float *final_T,
+                          int32_t *n_contrib, cudaStream_t s);
+void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
+                          const GRec *recs, const ViewGrads &g, const float *final_T,
+                          const int32_t *n_contrib, GGrad *g2d, cudaStream_t s);
+
+// Loss (Eq. 10-12) over one or more views (packed per view through the arrays).
+struct LossViews {
+    int n_views;
+    int W[kMaxViews], H[kMaxViews];
+    uint32_t tile_base[kMaxViews]; // first 16x16 loss tile of each view
+    uint32_t total_tiles;
+    const float *rgb[kMaxViews];
+    const float *depth[kMaxViews];
+    const float *gt[kMaxViews];
+    const float *lidar[kMaxViews];
+    float *d_rgb[kMaxViews];
+    float *d_depth[kMaxViews];
+    double *loss_out[kMaxViews];
+    float lambda_ssim, lambda_depth;
+    size_t gmap_base[kMaxViews]; // filled by launch_loss
+};
+size_t loss_tmp_bytes(const LossViews &lv);
+void launch_loss(const LossViews &lv, void *tmp, cudaStream_t s);
+
+void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, float *rgb_out,
+                         float *depth_out, cudaStream_t s);
+
+} // namespace lvigs

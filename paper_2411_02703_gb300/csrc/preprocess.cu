@@ -1,0 +1,571 @@
+// preprocess.cu -- per-Gaussian projection (a1) and its chain rule (a7).
+//
+// Forward, one thread per Gaussian looping over the views of the call:
+//   Sigma = R S S^T R^T (Eq. 2), the EWA projection Sigma_I = J Q Sigma Q^T J^T
+//   and mu_I = [Q, T] mu (Eq. 7), the 0.3 px^2 dilation, the conic, the 3-sigma
+//   radius and tile rectangle, opacity = sigmoid(logit) and the SH colour.
+// The quantities that decide the tile keys (view-space z, screen position,
+// radius, rectangle) are evaluated in strict IEEE binary32 with one rounding
+// per operation in a fixed order (the __f*_rn intrinsics are never
+// contracted), so the keys are reproducible bit for bit on any IEEE machine.
+//
+// Backward, one thread per Gaussian, accumulating over views in registers, so
+// the parameter gradients need no atomics.
+#include "lvigs_internal.cuh"
+
+namespace lvigs {
+namespace {
+
+#define RN_MUL __fmul_rn
+#define RN_ADD __fadd_rn
+#define RN_SUB __fsub_rn
+#define RN_DIV __fdiv_rn
+
+// Real spherical-harmonic normalisations (with the Condon-Shortley phase).
+constexpr float kY00 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+constexpr float kY1 = 0.48860251190291992f;   // sqrt(3 / (4 pi))
+constexpr float kY2a = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+constexpr float kY2b = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+constexpr float kY2c = 0.54627421529603959f;  // sqrt(15 / pi) / 4
+constexpr float kY3a = 0.59004358992664352f;  // sqrt(35 / (2 pi)) / 4
+constexpr float kY3b = 2.8906114426405538f;   // sqrt(105 / pi) / 2
+constexpr float kY3c = 0.45704579946446572f;  // sqrt(21 / (2 pi)) / 4
+constexpr float kY3d = 0.37317633259011540f;  // sqrt(7 / pi) / 4
+constexpr float kY3e = 1.4453057213202769f;   // sqrt(105 / pi) / 4
+
+// Basis values at the unit direction (x, y, z), index l^2 + l + m.
+__device__ __forceinline__ void sh_values(int deg, float x, float y, float z, float Y[16]) {
+    Y[0] = kY00;
+    if (deg < 1) return;
+    Y[1] = -kY1 * y;
+    Y[2] = kY1 * z;
+    Y[3] = -kY1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kY2a * x * y;
+    Y[5] = -kY2a * y * z;
+    Y[6] = kY2b * (2.f * zz - xx - yy);
+    Y[7] = -kY2a * x * z;
+    Y[8] = kY2c * (xx - yy);
+    if (deg < 3) return;
+    Y[9] = -kY3a * y * (3.f * xx - yy);
+    Y[10] = kY3b * x * y * z;
+    Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+    Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+    Y[14] = kY3e * z * (xx - yy);
+    Y[15] = -kY3a * x * (xx - 3.f * yy);
+}
+
+// sum_k w[k] * grad Y_k at (x, y, z), with the Cartesian gradient of each
+// basis polynomial (the projection onto the sphere is applied by the caller).
+__device__ __forceinline__ float3 sh_weighted_grad(int deg, float x, float y, float z,
+                                                   const float w[16]) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (deg >= 1) {
+        gy -= kY1 * w[1];
+        gz += kY1 * w[2];
+        gx -= kY1 * w[3];
+    }
+    if (deg >= 2) {
+        gx += kY2a * y * w[4];
+        gy += kY2a * x * w[4];
+        gy -= kY2a * z * w[5];
+        gz -= kY2a * y * w[5];
+        gx -= 2.f * kY2b * x * w[6];
+        gy -= 2.f * kY2b * y * w[6];
+        gz += 4.f * kY2b * z * w[6];
+        gx -= kY2a * z * w[7];
+        gz -= kY2a * x * w[7];
+        gx += 2.f * kY2c * x * w[8];
+        gy -= 2.f * kY2c * y * w[8];
+    }
+    if (deg >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        gx -= 6.f * kY3a * x * y * w[9];
+        gy -= 3.f * kY3a * (xx - yy) * w[9];
+        gx += kY3b * y * z * w[10];
+        gy += kY3b * x * z * w[10];
+        gz += kY3b * x * y * w[10];
+        gx += 2.f * kY3c * x * y * w[11];
+        gy -= kY3c * (4.f * zz - xx - 3.f * yy) * w[11];
+        gz -= 8.f * kY3c * y * z * w[11];
+        gx -= 6.f * kY3d * x * z * w[12];
+        gy -= 6.f * kY3d * y * z * w[12];
+        gz += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+        gx -= kY3c * (4.f * zz - 3.f * xx - yy) * w[13];
+        gy += 2.f * kY3c * x * y * w[13];
+        gz -= 8.f * kY3c * x * z * w[13];
+        gx += 2.f * kY3e * x * z * w[14];
+        gy -= 2.f * kY3e * y * z * w[14];
+        gz += kY3e * (xx - yy) * w[14];
+        gx -= 3.f * kY3a * (xx - yy) * w[15];
+        gy += 6.f * kY3a * x * y * w[15];
+    }
+    return make_float3(gx, gy, gz);
+}
+
+// Rotation of the unit quaternion (w, x, y, z), strict binary32.
+__device__ __forceinline__ void quat_rotation_strict(float w, float x, float y, float z, float r[9]) {
+    r[0] = RN_SUB(1.f, RN_MUL(2.f, RN_ADD(RN_MUL(y, y), RN_MUL(z, z))));
+    r[1] = RN_MUL(2.f, RN_SUB(RN_MUL(x, y), RN_MUL(w, z)));
+    r[2] = RN_MUL(2.f, RN_ADD(RN_MUL(x, z), RN_MUL(w, y)));
+    r[3] = RN_MUL(2.f, RN_ADD(RN_MUL(x, y), RN_MUL(w, z)));
+    r[4] = RN_SUB(1.f, RN_MUL(2.f, RN_ADD(RN_MUL(x, x), RN_MUL(z, z))));
+    r[5] = RN_MUL(2.f, RN_SUB(RN_MUL(y, z), RN_MUL(w, x)));
+    r[6] = RN_MUL(2.f, RN_SUB(RN_MUL(x, z), RN_MUL(w, y)));
+    r[7] = RN_MUL(2.f, RN_ADD(RN_MUL(y, z), RN_MUL(w, x)));
+    r[8] = RN_SUB(1.f, RN_MUL(2.f, RN_ADD(RN_MUL(x, x), RN_MUL(y, y))));
+}
+
+__device__ __forceinline__ float dot3_strict(float a0, float a1, float a2, float b0, float b1,
+                                             float b2) {
+    return RN_ADD(RN_ADD(RN_MUL(a0, b0), RN_MUL(a1, b1)), RN_MUL(a2, b2));
+}
+
+__device__ __forceinline__ float tile_coord(float f, int hi) {
+    if (!(f > 0.f)) return 0.f;
+    if (f > (float)hi) return (float)hi;
+    return f;
+}
+
+// Per-Gaussian, view-independent part: scales, unit quaternion, Sigma (strict).
+struct GaussLocal {
+    float s[3];
+    float qn[4];
+    float qnorm;
+    float r[9];
+    float S[6]; // Sigma00, 01, 02, 11, 12, 22
+    bool ok;
+};
+
+__device__ __forceinline__ void gauss_local_strict(const GaussParams &P, int g, GaussLocal &L) {
+    const float *ls = P.log_scales + 3 * (size_t)g;
+    const float *q = P.quats + 4 * (size_t)g;
+    // exp in binary64, one rounding to binary32
+    L.s[0] = __double2float_rn(exp((double)ls[0]));
+    L.s[1] = __double2float_rn(exp((double)ls[1]));
+    L.s[2] = __double2float_rn(exp((double)ls[2]));
+    const float q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+    float n2 = RN_MUL(q0, q0);
+    n2 = RN_ADD(n2, RN_MUL(q1, q1));
+    n2 = RN_ADD(n2, RN_MUL(q2, q2));
+    n2 = RN_ADD(n2, RN_MUL(q3, q3));
+    L.ok = n2 > 0.f;
+    const float nr = __fsqrt_rn(n2);
+    L.qnorm = nr;
+    L.qn[0] = RN_DIV(q0, nr);
+    L.qn[1] = RN_DIV(q1, nr);
+    L.qn[2] = RN_DIV(q2, nr);
+    L.qn[3] = RN_DIV(q3, nr);
+    quat_rotation_strict(L.qn[0], L.qn[1], L.qn[2], L.qn[3], L.r);
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = RN_MUL(L.r[3 * i + j], L.s[j]);
+    L.S[0] = dot3_strict(M[0], M[1], M[2], M[0], M[1], M[2]);
+    L.S[1] = dot3_strict(M[0], M[1], M[2], M[3], M[4], M[5]);
+    L.S[2] = dot3_strict(M[0], M[1], M[2], M[6], M[7], M[8]);
+    L.S[3] = dot3_strict(M[3], M[4], M[5], M[3], M[4], M[5]);
+    L.S[4] = dot3_strict(M[3], M[4], M[5], M[6], M[7], M[8]);
+    L.S[5] = dot3_strict(M[6], M[7], M[8], M[6], M[7], M[8]);
+}
+
+__device__ __forceinline__ float sig(const float S[6], int i, int j) {
+    // symmetric access into the 6 stored entries
+    const int lo = i < j ? i : j, hi = i < j ? j : i;
+    return S[lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)];
+}
+
+__global__ void __launch_bounds__(128)
+preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__restrict__ recs,
+                      uint32_t *__restrict__ tiles, uint32_t *__restrict__ zbits,
+                      uint2 *__restrict__ rects) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    const size_t N = (size_t)P.n;
+    GaussLocal L;
+    gauss_local_strict(P, g, L);
+    const float mx = P.means[3 * (size_t)g], my = P.means[3 * (size_t)g + 1],
+                mz = P.means[3 * (size_t)g + 2];
+    const float opacity = 1.f / (1.f + expf(-P.opacity_logits[g]));
+    const int deg = P.sh_degree;
+    const int nk = (deg + 1) * (deg + 1);
+    const float *shg = P.sh + (size_t)g * P.sh_stride_k * 3;
+    const float tw = (float)vsp->tile_w, th = (float)vsp->tile_h;
+    const int n_views = vsp->n_views;
+
+#pragma unroll 1
+    for (int vi = 0; vi < n_views; ++vi) {
+        const ViewDesc &V = vsp->v[vi];
+        const size_t o = (size_t)vi * N + g;
+        // mu_I = [Q_iw, T_iw] mu_W  (Eq. 7), strict
+        float px = RN_MUL(V.R[0], mx);
+        px = RN_ADD(px, RN_MUL(V.R[1], my));
+        px = RN_ADD(px, RN_MUL(V.R[2], mz));
+        px = RN_ADD(px, V.t[0]);
+        float py = RN_MUL(V.R[3], mx);
+        py = RN_ADD(py, RN_MUL(V.R[4], my));
+        py = RN_ADD(py, RN_MUL(V.R[5], mz));
+        py = RN_ADD(py, V.t[1]);
+        float pz = RN_MUL(V.R[6], mx);
+        pz = RN_ADD(pz, RN_MUL(V.R[7], my));
+        pz = RN_ADD(pz, RN_MUL(V.R[8], mz));
+        pz = RN_ADD(pz, V.t[2]);
+        bool vis = L.ok && (pz > 0.2f);
+        float a = 0.f, b = 0.f, c = 0.f, det = 0.f, u = 0.f, v = 0.f;
+        int rad = 0;
+        if (vis) {
+            const float xz = RN_DIV(px, pz), yz = RN_DIV(py, pz);
+            const float txc = xz < -V.limx ? -V.limx : (xz > V.limx ? V.limx : xz);
+            const float tyc = yz < -V.limy ? -V.limy : (yz > V.limy ? V.limy : yz);
+            const float J00 = RN_DIV(V.fx, pz);
+            const float J02 = RN_DIV(-RN_MUL(V.fx, txc), pz);
+            const float J11 = RN_DIV(V.fy, pz);
+            const float J12 = RN_DIV(-RN_MUL(V.fy, tyc), pz);
+            float T[6];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T[j] = RN_ADD(RN_MUL(J00, V.R[j]), RN_MUL(J02, V.R[6 + j]));
+                T[3 + j] = RN_ADD(RN_MUL(J11, V.R[3 + j]), RN_MUL(J12, V.R[6 + j]));
+            }
+            float U[6];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float acc = RN_MUL(T[3 * i], sig(L.S, 0, j));
+                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 1], sig(L.S, 1, j)));
+                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 2], sig(L.S, 2, j)));
+                    U[3 * i + j] = acc;
+                }
+            a = dot3_strict(U[0], U[1], U[2], T[0], T[1], T[2]);
+            b = dot3_strict(U[0], U[1], U[2], T[3], T[4], T[5]);
+            c = dot3_strict(U[3], U[4], U[5], T[3], T[4], T[5]);
+            a = RN_ADD(a, 0.3f);
+            c = RN_ADD(c, 0.3f);
+            det = RN_SUB(RN_MUL(a, c), RN_MUL(b, b));
+            vis = det > 0.f;
+            if (vis) {
+                const float mid = RN_MUL(0.5f, RN_ADD(a, c));
+                const float disc = RN_SUB(RN_MUL(mid, mid), det);
+                const float lam = RN_ADD(mid, __fsqrt_rn(disc > 0.1f ? disc : 0.1f));
+                rad = (int)ceilf(RN_MUL(3.f, __fsqrt_rn(lam)));
+                u = RN_ADD(RN_MUL(V.fx, xz), V.cx);
+                v = RN_ADD(RN_MUL(V.fy, yz), V.cy);
+            }
+        }
+        uint32_t ntiles = 0;
+        uint2 rect = make_uint2(0, 0);
+        if (vis) {
+            const float fr = (float)rad;
+            const int x0 = (int)tile_coord(RN_DIV(RN_SUB(u, fr), tw), V.tiles_x);
+            const int x1 = (int)tile_coord(RN_DIV(RN_ADD(RN_ADD(u, fr), tw - 1.f), tw), V.tiles_x);
+            const int y0 = (int)tile_coord(RN_DIV(RN_SUB(v, fr), th), V.tiles_y);
+            const int y1 = (int)tile_coord(RN_DIV(RN_ADD(RN_ADD(v, fr), th - 1.f), th), V.tiles_y);
+            ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
+            rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
+        }
+        tiles[o] = ntiles;
+        zbits[o] = __float_as_uint(pz);
+        rects[o] = rect;
+        if (ntiles == 0) continue;
+        // values composited (binary32; not part of the key)
+        const float inv_det = 1.f / det;
+        // colour: SH at the direction from the camera centre to the mean
+        float dx = mx - V.campos[0], dy = my - V.campos[1], dz = mz - V.campos[2];
+        const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inv_len;
+        dy *= inv_len;
+        dz *= inv_len;
+        float Y[16];
+        sh_values(deg, dx, dy, dz, Y);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nk) acc += Y[k] * __ldg(shg + 3 * k + ch);
+            rgb[ch] = fmaxf(acc, 0.f);
+        }
+        GRec rec;
+        rec.a = make_float4(u, v, c * inv_det, -b * inv_det);
+        rec.b = make_float4(a * inv_det, opacity, pz, 0.f);
+        rec.c = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+        recs[o] = rec;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward (a7): chain rule from the screen-space gradients of every view.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ tiles,
+                      const GGrad *__restrict__ g2d, ParamGrads G) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    const size_t N = (size_t)P.n;
+    const int deg = P.sh_degree;
+    const int nk = (deg + 1) * (deg + 1);
+    const int K = P.sh_stride_k;
+    const float *shg = P.sh + (size_t)g * K * 3;
+
+    float d_mean[3] = {0.f, 0.f, 0.f};
+    float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; // symmetric dL/dSigma (00,01,02,11,12,22)
+    float d_op = 0.f;
+    float d_sh[16][3];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) d_sh[k][0] = d_sh[k][1] = d_sh[k][2] = 0.f;
+    bool any = false;
+
+    const float mx = P.means[3 * (size_t)g], my = P.means[3 * (size_t)g + 1],
+                mz = P.means[3 * (size_t)g + 2];
+    const float *ls = P.log_scales + 3 * (size_t)g;
+    const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    const float *q = P.quats + 4 * (size_t)g;
+    const float qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float qi = 1.f / qnorm;
+    const float qw = q[0] * qi, qx = q[1] * qi, qy = q[2] * qi, qz = q[3] * qi;
+    float r[9];
+    r[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    r[1] = 2.f * (qx * qy - qw * qz);
+    r[2] = 2.f * (qx * qz + qw * qy);
+    r[3] = 2.f * (qx * qy + qw * qz);
+    r[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    r[5] = 2.f * (qy * qz - qw * qx);
+    r[6] = 2.f * (qx * qz - qw * qy);
+    r[7] = 2.f * (qy * qz + qw * qx);
+    r[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    float M[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = r[3 * i + j] * s[j];
+    float Sg[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Sg[i][j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+
+    const int n_views = vsp->n_views;
+#pragma unroll 1
+    for (int vi = 0; vi < n_views; ++vi) {
+        const size_t o = (size_t)vi * N + g;
+        if (tiles[o] == 0) continue;
+        const GGrad gg = g2d[o];
+        const float du = gg.g0.x, dv = gg.g0.y, dA = gg.g0.z, dB = gg.g0.w;
+        const float dC = gg.g1.x, dop = gg.g1.y, ddepth = gg.g1.z;
+        const float drgb[3] = {gg.g2.x, gg.g2.y, gg.g2.z};
+        if (du == 0.f && dv == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && dop == 0.f &&
+            ddepth == 0.f && drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f)
+            continue;
+        any = true;
+        const ViewDesc &V = vsp->v[vi];
+        const float px = V.R[0] * mx + V.R[1] * my + V.R[2] * mz + V.t[0];
+        const float py = V.R[3] * mx + V.R[4] * my + V.R[5] * mz + V.t[1];
+        const float pz = V.R[6] * mx + V.R[7] * my + V.R[8] * mz + V.t[2];
+        const float iz = 1.f / pz;
+        const float xz = px * iz, yz = py * iz;
+        const bool clx = xz < -V.limx || xz > V.limx;
+        const bool cly = yz < -V.limy || yz > V.limy;
+        const float txc = fminf(V.limx, fmaxf(-V.limx, xz));
+        const float tyc = fminf(V.limy, fmaxf(-V.limy, yz));
+        const float J00 = V.fx * iz, J02 = -V.fx * txc * iz;
+        const float J11 = V.fy * iz, J12 = -V.fy * tyc * iz;
+        float T[2][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T[0][j] = J00 * V.R[j] + J02 * V.R[6 + j];
+            T[1][j] = J11 * V.R[3 + j] + J12 * V.R[6 + j];
+        }
+        float ST[2][3]; // Sigma T_i^T
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+                ST[i][rr] = Sg[rr][0] * T[i][0] + Sg[rr][1] * T[i][1] + Sg[rr][2] * T[i][2];
+        const float a = T[0][0] * ST[0][0] + T[0][1] * ST[0][1] + T[0][2] * ST[0][2] + 0.3f;
+        const float b = T[0][0] * ST[1][0] + T[0][1] * ST[1][1] + T[0][2] * ST[1][2];
+        const float c = T[1][0] * ST[1][0] + T[1][1] * ST[1][1] + T[1][2] * ST[1][2] + 0.3f;
+        const float det = a * c - b * b;
+        const float id = 1.f / det, id2 = id * id;
+        // conic (A, B, C) = (c, -b, a) / det
+        const float da = -c * c * id2 * dA + b * c * id2 * dB + (id - a * c * id2) * dC;
+        const float dc = (id - a * c * id2) * dA + a * b * id2 * dB - a * a * id2 * dC;
+        const float db = 2.f * b * c * id2 * dA + (-id - 2.f * b * b * id2) * dB + 2.f * a * b * id2 * dC;
+        // a = T0 Sigma T0^T, b = T0 Sigma T1^T, c = T1 Sigma T1^T
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int ss = rr; ss < 3; ++ss) {
+                float v = da * T[0][rr] * T[0][ss] + dc * T[1][rr] * T[1][ss] +
+                          0.5f * db * (T[0][rr] * T[1][ss] + T[1][rr] * T[0][ss]);
+                // off-diagonal entries collect both symmetric positions
+                if (ss != rr) v *= 2.f;
+                dSig[rr == 0 ? ss : (rr == 1 ? 2 + ss : 5)] += v;
+            }
+        float dT[2][3];
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+            dT[0][rr] = 2.f * da * ST[0][rr] + db * ST[1][rr];
+            dT[1][rr] = db * ST[0][rr] + 2.f * dc * ST[1][rr];
+        }
+        float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dJ00 += dT[0][j] * V.R[j];
+            dJ02 += dT[0][j] * V.R[6 + j];
+            dJ11 += dT[1][j] * V.R[3 + j];
+            dJ12 += dT[1][j] * V.R[6 + j];
+        }
+        const float iz2 = iz * iz;
+        float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+        dpz -= (dJ00 * V.fx + dJ11 * V.fy) * iz2;
+        if (clx) {
+            dpz += dJ02 * V.fx * txc * iz2;
+        } else {
+            dpx -= dJ02 * V.fx * iz2;
+            dpz += dJ02 * 2.f * V.fx * px * iz2 * iz;
+        }
+        if (cly) {
+            dpz += dJ12 * V.fy * tyc * iz2;
+        } else {
+            dpy -= dJ12 * V.fy * iz2;
+            dpz += dJ12 * 2.f * V.fy * py * iz2 * iz;
+        }
+        // screen position and depth
+        dpx += du * V.fx * iz;
+        dpy += dv * V.fy * iz;
+        dpz += -(du * V.fx * px + dv * V.fy * py) * iz2 + ddepth;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d_mean[k] += V.R[k] * dpx + V.R[3 + k] * dpy + V.R[6 + k] * dpz;
+        // opacity
+        d_op += dop;
+        // colour through the SH basis at the view direction
+        float ex = mx - V.campos[0], ey = my - V.campos[1], ez = mz - V.campos[2];
+        const float len = sqrtf(ex * ex + ey * ey + ez * ez);
+        const float il = 1.f / len;
+        ex *= il;
+        ey *= il;
+        ez *= il;
+        float Y[16];
+        sh_values(deg, ex, ey, ez, Y);
+        float w[16];
+        float m3[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float raw = 0.5f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                if (k < nk) raw += Y[k] * __ldg(shg + 3 * k + ch);
+            m3[ch] = raw < 0.f ? 0.f : drgb[ch];
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            w[k] = 0.f;
+            if (k < nk) {
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    d_sh[k][ch] += Y[k] * m3[ch];
+                    w[k] += m3[ch] * __ldg(shg + 3 * k + ch);
+                }
+            }
+        }
+        const float3 gd = sh_weighted_grad(deg, ex, ey, ez, w);
+        const float dd = gd.x * ex + gd.y * ey + gd.z * ez;
+        d_mean[0] += (gd.x - ex * dd) * il;
+        d_mean[1] += (gd.y - ey * dd) * il;
+        d_mean[2] += (gd.z - ez * dd) * il;
+    }
+
+    // Sigma = M M^T with M = R diag(s): dM = 2 dSigma_sym M
+    float dS[3][3];
+    dS[0][0] = dSig[0];
+    dS[1][1] = dSig[3];
+    dS[2][2] = dSig[5];
+    dS[0][1] = dS[1][0] = 0.5f * dSig[1];
+    dS[0][2] = dS[2][0] = 0.5f * dSig[2];
+    dS[1][2] = dS[2][1] = 0.5f * dSig[4];
+    float d_ls[3], dR[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float dsj = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float dMij = 2.f * (dS[i][0] * M[j] + dS[i][1] * M[3 + j] + dS[i][2] * M[6 + j]);
+            dsj += dMij * r[3 * i + j];
+            dR[3 * i + j] = dMij * s[j];
+        }
+        d_ls[j] = dsj * s[j];
+    }
+    float dq[4];
+    dq[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+    dq[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
+                   qw * dR[7] - 2.f * qx * dR[8]);
+    dq[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
+                   qz * dR[7] - 2.f * qy * dR[8]);
+    dq[3] = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
+                   qy * dR[5] + qx * dR[6] + qy * dR[7]);
+    const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
+    const float qn[4] = {qw, qx, qy, qz};
+    const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
+    const float d_logit = d_op * o * (1.f - o);
+
+    if (!G.accumulate) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G.d_means[3 * (size_t)g + k] = d_mean[k];
+            G.d_log_scales[3 * (size_t)g + k] = d_ls[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G.d_quats[4 * (size_t)g + k] = (dq[k] - qn[k] * qdot) * qi;
+        G.d_opacity_logits[g] = d_logit;
+        float *dsh = G.d_sh + (size_t)g * K * 3;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = d_sh[k][ch];
+        for (int k = 16; k < K; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = 0.f;
+    } else if (any) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G.d_means[3 * (size_t)g + k] += d_mean[k];
+            G.d_log_scales[3 * (size_t)g + k] += d_ls[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G.d_quats[4 * (size_t)g + k] += (dq[k] - qn[k] * qdot) * qi;
+        G.d_opacity_logits[g] += d_logit;
+        float *dsh = G.d_sh + (size_t)g * K * 3;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < nk)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += d_sh[k][ch];
+    }
+}
+
+} // namespace
+
+void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs, GRec *recs, uint32_t *tiles,
+                           uint32_t *zbits, uint2 *rects, cudaStream_t s) {
+    if (P.n <= 0) return;
+    const int threads = 128;
+    const int blocks = (P.n + threads - 1) / threads;
+    preprocess_fwd_kernel<<<blocks, threads, 0, s>>>(P, vs, recs, tiles, zbits, rects);
+}
+
+void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs, const uint32_t *tiles,
+                           const GGrad *g2d, const ParamGrads &G, cudaStream_t s) {
+    if (P.n <= 0) return;
+    const int threads = 128;
+    const int blocks = (P.n + threads - 1) / threads;
+    preprocess_bwd_kernel<<<blocks, threads, 0, s>>>(P, vs, tiles, g2d, G);
+}
+
+} // namespace lvigs

@@ -1,0 +1,427 @@
+// sort.cu -- tile-key expansion, device radix sort and tile ranges (a2-a4).
+//
+// The (tile, depth) order of the instance list is produced in two stable
+// sorts instead of one 64-bit sort:
+//   1. the visible (view, Gaussian) items are compacted (index order) and
+//      radix-sorted by the binary32 bits of their view-space depth;
+//   2. each item emits its (tile id, item) instances in that depth order, and
+//      the instances are radix-sorted by tile id only.
+// Stability makes the result equal to a sort by (tile id, depth bits, item
+// index): the unique order of the 64-bit keys (tile << 32 | depth bits).
+// Only ceil(log2(total tiles)) bits are sorted over the (large) instance
+// list, instead of 32 + that many.
+//
+// Every kernel reads its item count from device memory, so a whole step can
+// be captured in a CUDA graph without a host round trip; grids are sized by
+// host-side upper bounds.
+#include <algorithm>
+
+#include "lvigs_internal.cuh"
+
+namespace lvigs {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems; // 4096
+
+constexpr int kRsWarps = 8;
+constexpr int kRsThreads = kRsWarps * 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems; // 4096
+constexpr int kRsMaxGrid = 1024;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+// Returns the exclusive prefix; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t *total) {
+    __shared__ uint32_t warp_sums[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    uint32_t warp_off = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t s = warp_sums[w];
+        if (w < warp) warp_off += s;
+        tot += s;
+    }
+    __syncthreads();
+    *total = tot;
+    return warp_off + inc - x;
+}
+
+__device__ __forceinline__ uint32_t scan_item(const uint32_t *in, const uint32_t *gather,
+                                              int flag_only, uint32_t i) {
+    const uint32_t v = in[gather ? gather[i] : i];
+    return flag_only ? (v != 0u) : v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_reduce_kernel(const uint32_t *in, const uint32_t *gather, int flag_only, const uint32_t *n_dev,
+                   uint32_t n_host, uint32_t *block_sums) {
+    const uint32_t n = n_dev ? *n_dev : n_host;
+    const uint32_t begin = blockIdx.x * (uint32_t)kScanTile;
+    uint32_t sum = 0;
+    if (begin < n) {
+        const uint32_t end = min(begin + (uint32_t)kScanTile, n);
+        for (uint32_t i = begin + threadIdx.x; i < end; i += kScanThreads)
+            sum += scan_item(in, gather, flag_only, i);
+    }
+    uint32_t tot;
+    block_exclusive_scan_256(sum, &tot);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums by a single block; writes the grand total.
+__global__ void __launch_bounds__(kScanThreads)
+scan_blocks_kernel(uint32_t *block_sums, uint32_t nb, uint32_t *out_total) {
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += kScanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t x = i < nb ? block_sums[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(x, &tot);
+        if (i < nb) block_sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && out_total) *out_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_down_kernel(const uint32_t *in, const uint32_t *gather, int flag_only, const uint32_t *n_dev,
+                 uint32_t n_host, const uint32_t *block_offsets, uint32_t *out) {
+    const uint32_t n = n_dev ? *n_dev : n_host;
+    const uint32_t begin = blockIdx.x * (uint32_t)kScanTile;
+    if (begin >= n) return;
+    const uint32_t end = min(begin + (uint32_t)kScanTile, n);
+    uint32_t carry = block_offsets[blockIdx.x];
+    for (uint32_t base = begin; base < end; base += kScanThreads) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t x = i < end ? scan_item(in, gather, flag_only, i) : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(x, &tot);
+        if (i < end) out[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void compact_kernel(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
+                               uint32_t *keys, uint32_t *vals, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (tiles[i] != 0u) {
+            const uint32_t p = pos[i];
+            keys[p] = zbits[i];
+            vals[p] = i;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, reduce-then-scan per pass.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void rs_chunk(uint32_t n, int G, int b, uint32_t &begin, uint32_t &end) {
+    uint32_t per = (n + G - 1) / G;
+    per = (per + kRsTile - 1) / kRsTile * kRsTile;
+    const uint64_t bb = (uint64_t)b * per;
+    begin = bb < n ? (uint32_t)bb : n;
+    end = (uint64_t)begin + per < n ? begin + per : n;
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+radix_upsweep_kernel(const uint32_t *keys, const uint32_t *n_dev, int shift, int G,
+                     uint32_t *counts) {
+    __shared__ uint32_t hist[kRsWarps][256];
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t n = *n_dev;
+    uint32_t begin, end;
+    rs_chunk(n, G, blockIdx.x, begin, end);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t i0 = begin + warp * 32; i0 < end; i0 += kRsThreads) {
+        const uint32_t i = i0 + lane;
+        const bool valid = i < end;
+        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) hist[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRsWarps; ++w) s += hist[w][d];
+    counts[(size_t)d * G + blockIdx.x] = s;
+}
+
+// One block per digit: exclusive scan of the digit's per-block counts, in place.
+__global__ void __launch_bounds__(1024)
+radix_rowscan_kernel(uint32_t *counts, int G, uint32_t *totals) {
+    __shared__ uint32_t warp_sums[32];
+    const int d = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t x = t < G ? counts[(size_t)d * G + t] : 0u;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t ws = warp_sums[lane];
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_sums[lane] = wi - ws;
+        if (lane == 31) totals[d] = wi;
+    }
+    __syncthreads();
+    if (t < G) counts[(size_t)d * G + t] = warp_sums[warp] + inc - x;
+}
+
+__global__ void __launch_bounds__(kRsThreads)
+radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                       uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                       const uint32_t *n_dev, int shift, int G, const uint32_t *counts,
+                       const uint32_t *totals) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_hist[kRsWarps][256];
+    __shared__ uint32_t s_tile[256];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    {
+        uint32_t tot;
+        const uint32_t dp = block_exclusive_scan_256(totals[t], &tot);
+        s_base[t] = dp + counts[(size_t)t * G + blockIdx.x];
+    }
+    const uint32_t n = *n_dev;
+    uint32_t begin, end;
+    rs_chunk(n, G, blockIdx.x, begin, end);
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t tile0 = begin; tile0 < end; tile0 += kRsTile) {
+#pragma unroll
+        for (int w = 0; w < kRsWarps; ++w) s_hist[w][t] = 0;
+        __syncthreads();
+        uint32_t k[kRsItems], v[kRsItems], rank[kRsItems], d[kRsItems];
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t i = tile0 + warp * (kRsItems * 32) + j * 32 + lane;
+            const bool valid = i < end;
+            k[j] = valid ? keys_in[i] : 0u;
+            v[j] = valid ? vals_in[i] : 0u;
+            d[j] = valid ? (k[j] >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
+            uint32_t c = 0;
+            if (d[j] < 256u) c = s_hist[warp][d[j]];
+            rank[j] = c + __popc(peers & lt);
+            __syncwarp();
+            if (d[j] < 256u && lane == __ffs(peers) - 1) s_hist[warp][d[j]] = c + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kRsWarps; ++w) {
+                const uint32_t c = s_hist[w][t];
+                s_hist[w][t] = run;
+                run += c;
+            }
+            s_tile[t] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            if (d[j] < 256u) {
+                const uint32_t dest = s_base[d[j]] + s_hist[warp][d[j]] + rank[j];
+                keys_out[dest] = k[j];
+                vals_out[dest] = v[j];
+            }
+        }
+        __syncthreads();
+        s_base[t] += s_tile[t];
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------
+// Instance emission, ranges, debug keys.
+// --------------------------------------------------------------------------
+__global__ void emit_kernel(const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ sorted_idx,
+                            const uint32_t *__restrict__ offsets, const uint32_t *n_vis_dev,
+                            const uint2 *__restrict__ rects, uint32_t n_gauss,
+                            uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ inst_vals,
+                            uint64_t m_cap, uint32_t *status) {
+    const uint32_t n = *n_vis_dev;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint32_t idx = sorted_idx[j];
+        const uint32_t vi = idx / n_gauss;
+        const uint2 rc = rects[idx];
+        const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
+        const uint32_t base = vsp->v[vi].tile_base;
+        const uint32_t tx_n = (uint32_t)vsp->v[vi].tiles_x;
+        uint64_t pos = offsets[j];
+        const uint64_t cnt = (uint64_t)(x1 - x0) * (y1 - y0);
+        if (pos + cnt > m_cap) {
+            atomicOr(status, kStatusCapacity);
+            continue;
+        }
+        for (uint32_t ty = y0; ty < y1; ++ty)
+            for (uint32_t tx = x0; tx < x1; ++tx) {
+                tile_ids[pos] = base + ty * tx_n + tx;
+                inst_vals[pos] = idx;
+                ++pos;
+            }
+    }
+}
+
+__global__ void ranges_kernel(const uint32_t *__restrict__ tile_ids, const uint32_t *m_dev,
+                              uint32_t m_cap, uint2 *__restrict__ ranges) {
+    const uint32_t m = min(*m_dev, m_cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const uint32_t t = tile_ids[i];
+        if (i == 0 || tile_ids[i - 1] != t) ranges[t].x = i;
+        if (i == m - 1 || tile_ids[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+__global__ void clamp_count_kernel(const uint32_t *m_dev, uint32_t m_cap, uint32_t *out) {
+    const uint32_t m = *m_dev;
+    *out = m < m_cap ? m : m_cap;
+}
+
+__global__ void debug_keys_kernel(const uint32_t *tile_ids, const uint32_t *inst_vals,
+                                  const uint32_t *zbits, uint32_t n_gauss, uint64_t *keys,
+                                  uint32_t *vals, uint32_t m) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const uint32_t idx = inst_vals[i];
+        keys[i] = ((uint64_t)tile_ids[i] << 32) | zbits[idx];
+        vals[i] = idx % n_gauss;
+    }
+}
+
+__global__ void sum_i32_kernel(const int32_t *x, uint32_t n, unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += (uint32_t)x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+int rs_grid(int64_t n_max) {
+    int64_t g = (n_max + kRsTile - 1) / kRsTile;
+    if (g < 1) g = 1;
+    if (g > kRsMaxGrid) g = kRsMaxGrid;
+    return (int)g;
+}
+
+int grid_stride_blocks(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = 152 * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+} // namespace
+
+size_t scan_tmp_words(int64_t n_max) { return (size_t)((n_max + kScanTile - 1) / kScanTile) + 1; }
+
+void launch_scan(const uint32_t *in, const uint32_t *gather, int flag_only, uint32_t *out,
+                 uint32_t *out_total, const uint32_t *n_dev, int64_t n_max, uint32_t *tmp,
+                 cudaStream_t s) {
+    const uint32_t nb = (uint32_t)((n_max + kScanTile - 1) / kScanTile);
+    if (nb == 0) {
+        if (out_total) cudaMemsetAsync(out_total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, gather, flag_only, n_dev, (uint32_t)n_max, tmp);
+    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(tmp, nb, out_total);
+    scan_down_kernel<<<nb, kScanThreads, 0, s>>>(in, gather, flag_only, n_dev, (uint32_t)n_max, tmp, out);
+}
+
+void launch_compact(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
+                    uint32_t *keys, uint32_t *vals, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    compact_kernel<<<grid_stride_blocks(n, 256), 256, 0, s>>>(tiles, zbits, pos, keys, vals, (uint32_t)n);
+}
+
+size_t radix_tmp_words(int64_t n_max) { return (size_t)256 * rs_grid(n_max) + 256; }
+
+int launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                      const uint32_t *n_dev, int64_t n_max, int bits, uint32_t *tmp,
+                      cudaStream_t s) {
+    if (n_max <= 0 || bits <= 0) return 0;
+    const int G = rs_grid(n_max);
+    uint32_t *counts = tmp;
+    uint32_t *totals = tmp + (size_t)256 * G;
+    const int passes = std::min((bits + 7) / 8, 4);
+    uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        radix_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, n_dev, shift, G, counts);
+        radix_rowscan_kernel<<<256, 1024, 0, s>>>(counts, G, totals);
+        radix_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, G, counts, totals);
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    return passes & 1; // 1: the sorted pairs are in keys_alt / vals_alt
+}
+
+void launch_emit(const ViewSet *vs, const uint32_t *sorted_idx, const uint32_t *offsets,
+                 const uint32_t *n_vis_dev, const uint2 *rects, int n_gauss, uint32_t *tile_ids,
+                 uint32_t *inst_vals, int64_t m_cap, int64_t n_max, uint32_t *status,
+                 cudaStream_t s) {
+    if (n_max <= 0) return;
+    emit_kernel<<<grid_stride_blocks(n_max, 256), 256, 0, s>>>(vs, sorted_idx, offsets, n_vis_dev, rects,
+                                                                (uint32_t)n_gauss, tile_ids, inst_vals,
+                                                                (uint64_t)m_cap, status);
+}
+
+void launch_ranges(const uint32_t *tile_ids, const uint32_t *m_dev, int64_t m_cap,
+                   uint2 *ranges, uint32_t total_tiles, cudaStream_t s) {
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, s);
+    if (m_cap <= 0) return;
+    ranges_kernel<<<grid_stride_blocks(m_cap, 256), 256, 0, s>>>(tile_ids, m_dev, (uint32_t)m_cap, ranges);
+}
+
+void launch_clamp_count(const uint32_t *m_dev, int64_t m_cap, uint32_t *out, cudaStream_t s) {
+    clamp_count_kernel<<<1, 1, 0, s>>>(m_dev, (uint32_t)(m_cap < 0xffffffffLL ? m_cap : 0xffffffffLL), out);
+}
+
+void launch_sum_i32(const int32_t *x, uint32_t n, unsigned long long *out, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (n == 0) return;
+    sum_i32_kernel<<<grid_stride_blocks(n, 256), 256, 0, s>>>(x, n, out);
+}
+
+void launch_debug_keys(const uint32_t *tile_ids, const uint32_t *inst_vals, const uint32_t *zbits,
+                       int n_gauss, uint64_t *keys, uint32_t *vals, int64_t m, cudaStream_t s) {
+    if (m <= 0) return;
+    debug_keys_kernel<<<grid_stride_blocks(m, 256), 256, 0, s>>>(tile_ids, inst_vals, zbits,
+                                                                  (uint32_t)n_gauss, keys, vals, (uint32_t)m);
+}
+
+} // namespace lvigs
