@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--batch-depth", type=int, default=0)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     return ap.parse_args()
@@ -111,10 +112,11 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-def algorithmic_bytes(N, V, K, n_vis, M, P, loaded):
+def algorithmic_bytes(N, V, K, n_vis, M, P, loaded, pyr_px=0):
     """Bytes each phase must move (float32 = 4 B), from the step's counts."""
     prm = N * 4 * (11 + 3 * K)
     return {
+        "pyramid": pyr_px * 20,
         "preprocess": prm + V * N * 16 + n_vis * 48,
         "compact": V * N * 8 + n_vis * 8,
         "depth_sort": 4 * 20 * n_vis,
@@ -161,7 +163,7 @@ def run_ours(args):
     lis = [torch.from_numpy(g).cuda() for g in wl["lidars"]]
     gts_h = [torch.from_numpy(g).pin_memory() for g in wl["gts"]]
     lis_h = [torch.from_numpy(g).pin_memory() for g in wl["lidars"]]
-    lv = P.Context(tile=tile)
+    lv = P.Context(tile=tile, batch_depth=args.batch_depth)
     grads = {k: torch.zeros_like(dev[k]) for k in P.PARAM_NAMES}
     N = params["means"].shape[0]
     V = len(cams)
@@ -266,7 +268,9 @@ def run_ours(args):
 
     n_vis, M, nc_sum, P_px = stats
     # instances the compositing kernels gather: bounded by M; use M (upper bound)
-    ab = algorithmic_bytes(N, V, K, n_vis, M, P_px, M)
+    # pyramid: each level-down reads rgb + depth (16 B) and writes a quarter of it
+    pyr_px = sum(sum((c.W >> i) * (c.H >> i) for i in range(l)) for c, l in zip(cams, levels))
+    ab = algorithmic_bytes(N, V, K, n_vis, M, P_px, M, pyr_px)
     flops = alu_flops(nc_sum)
     hbm_peak, sm_max, peak_kind = peaks()
     dominant = max(phase_ms, key=lambda k: phase_ms[k])
@@ -301,6 +305,7 @@ def run_ours(args):
         "data": "synthetic (seeded LiDAR-sweep scene and procedural targets)",
         "config": {"workload": args.workload, "gaussians": N, "views": V, "levels": levels,
                    "base_resolution": "1280x1024", "sh_degree": int(params["sh_degree"]), "tile": args.tile,
+                   "batch_depth": args.batch_depth or "auto",
                    "loss": "0.8 L1 + 0.2 (1-SSIM) + 0.1 depth L1", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (236 MB of parameters per step)"},
         "mpix_per_s": round(world * pix * steps_per_s / 1e6, 3),

@@ -62,7 +62,7 @@ typedef struct lvigs_ctx lvigs_ctx;
  * results depend on it; batch_depth does not change results. */
 typedef struct {
     int tile_w, tile_h;         /* 16x16 (default), 8x8 or 32x16 */
-    int batch_depth;            /* Gaussians staged in shared memory per round; 0 = auto */
+    int batch_depth;            /* Gaussians each compositing warp stages per round: 0 (auto), 32 or 64 */
     size_t max_workspace_bytes; /* 0 = no cap; else LVIGS_ERR_CAPACITY beyond it */
 } lvigs_config;
 

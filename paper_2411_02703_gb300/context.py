@@ -62,9 +62,9 @@ def level_size(cam, level):
 class Context:
     """One library context (workspace, view slots, batched-step graph)."""
 
-    def __init__(self, tile=(16, 16), max_workspace_bytes=0):
+    def __init__(self, tile=(16, 16), max_workspace_bytes=0, batch_depth=0):
         self._lib = L.load()
-        cfg = L.Config(int(tile[0]), int(tile[1]), 0, int(max_workspace_bytes))
+        cfg = L.Config(int(tile[0]), int(tile[1]), int(batch_depth), int(max_workspace_bytes))
         self._h = ctypes.c_void_p()
         L.check(self._lib.lvigs_create(ctypes.byref(self._h), ctypes.byref(cfg)), "lvigs_create")
         self.tile = (int(tile[0]), int(tile[1]))

@@ -48,6 +48,7 @@ struct BatchKey {
 
 struct lvigs_ctx {
     lvigs_config cfg{};
+    int bm = 2; // Gaussians staged per compositing round = bm x threads
     int device = 0;
     std::string err;
     size_t bytes_in_use = 0;
@@ -391,9 +392,13 @@ lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
     lvigs_config_default(&c);
     if (cfg) c = *cfg;
     if (!tile_supported(c.tile_w, c.tile_h)) return LVIGS_ERR_INVALID_ARG;
-    if (c.batch_depth != 0 && c.batch_depth != c.tile_w * c.tile_h) return LVIGS_ERR_INVALID_ARG;
+    // compositing warps stage 32 (bm = 1) or 64 (bm = 2) Gaussians per round
+    int bm = 2;
+    if (c.batch_depth == 32) bm = 1;
+    else if (c.batch_depth != 0 && c.batch_depth != 64) return LVIGS_ERR_INVALID_ARG;
     lvigs_ctx *ctx = new lvigs_ctx();
     ctx->cfg = c;
+    ctx->bm = bm;
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_counters, 4 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_status, sizeof(uint32_t));
@@ -503,7 +508,7 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
-                             (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s);
+                             (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s, ctx->bm);
     }
     LV_CUDA(cudaGetLastError());
     st.valid = true;
@@ -533,7 +538,7 @@ lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
         launch_composite_bwd(st->vs, (const ViewSet *)st->vs_dev.p, (const uint2 *)st->ranges.p, st->sorted_vals(),
                              (const GRec *)st->recs.p, vg, (const float *)st->final_T.p,
-                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, s);
+                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, s, ctx->bm);
     }
     ParamGrads G{grads->d_means, grads->d_log_scales, grads->d_quats, grads->d_opacity_logits, grads->d_sh,
                  grads->accumulate};
@@ -781,7 +786,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
-                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s);
+                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s, ctx->bm);
     }
     // 4. a8: loss and its image gradients for every view
     {
@@ -801,7 +806,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
         launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
-                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, s);
+                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, s, ctx->bm);
     }
     ParamGrads G{gr->d_means, gr->d_log_scales, gr->d_quats, gr->d_opacity_logits, gr->d_sh, gr->accumulate};
     {

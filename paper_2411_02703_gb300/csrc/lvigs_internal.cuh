@@ -61,8 +61,9 @@ struct ParamGrads {
 };
 
 // Screen-space record of one (view, Gaussian), written by preprocessing and
-// gathered by the compositing kernels: a = (u, v, A, B), b = (C, opacity, z, -),
-// c = (r, g, b, -), with the conic [[A, B], [B, C]].
+// gathered by the compositing kernels: a = (u, v, A, B), b = (C, opacity, z, ex),
+// c = (r, g, b, ey), with the conic [[A, B], [B, C]] and (ex, ey) the
+// half-extents of a box that holds every pixel where alpha can reach 1/255.
 struct __align__(16) GRec {
     float4 a, b, c;
 };
@@ -132,12 +133,14 @@ void launch_clamp_count(const uint32_t *m_dev, int64_t m_cap, uint32_t *out, cud
 void launch_debug_keys(const uint32_t *tile_ids, const uint32_t *inst_vals, const uint32_t *zbits,
                        int n_gauss, uint64_t *keys, uint32_t *vals, int64_t m, cudaStream_t s);
 
+// Compositing: one warp per 8x8 pixel block (tile_w * tile_h / 2 threads per
+// CTA); each warp stages 32 * bm Gaussians per round (bm = 1 or 2).
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T,
-                          int32_t *n_contrib, cudaStream_t s);
+                          int32_t *n_contrib, cudaStream_t s, int bm);
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewGrads &g, const float *final_T,
-                          const int32_t *n_contrib, GGrad *g2d, cudaStream_t s);
+                          const int32_t *n_contrib, GGrad *g2d, cudaStream_t s, int bm);
 
 // Loss (Eq. 10-12) over one or more views (packed per view through the arrays).
 struct LossViews {

@@ -290,10 +290,19 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
                 if (k < nk) acc += Y[k] * __ldg(shg + 3 * k + ch);
             rgb[ch] = fmaxf(acc, 0.f);
         }
+        // half-extents of the box where o exp(power) can reach 1/255: the
+        // ellipse d^T Sigma_I^{-1} d <= 2 (ln(255 o) + 0.1), widened by 0.05 px;
+        // the margin is far above the binary32 rounding of the compositing test
+        float ex = -1e30f, ey = -1e30f;
+        if (opacity * 255.f >= 1.f) {
+            const float tau = logf(255.f * opacity) + 0.1f;
+            ex = (a > 0.f) ? sqrtf(2.f * tau * a) + 0.05f : 1e30f;
+            ey = (c > 0.f) ? sqrtf(2.f * tau * c) + 0.05f : 1e30f;
+        }
         GRec rec;
         rec.a = make_float4(u, v, c * inv_det, -b * inv_det);
-        rec.b = make_float4(a * inv_det, opacity, pz, 0.f);
-        rec.c = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+        rec.b = make_float4(a * inv_det, opacity, pz, ex);
+        rec.c = make_float4(rgb[0], rgb[1], rgb[2], ey);
         recs[o] = rec;
     }
 }
