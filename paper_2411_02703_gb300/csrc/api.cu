@@ -23,10 +23,15 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Tile lists longer than this are composited by several warps in parallel.
+constexpr int kChunkLen = 1024;
+
 struct RenderState {
     DevBuf recs, tiles, zbits, rects;
     DevBuf inst_a_t, inst_a_v, inst_b_t, inst_b_v;
     DevBuf ranges, final_T, n_contrib, vs_dev, counters;
+    DevBuf n_chunks, chunk_base, n_slots, part_base, pair_tile, part; // list-parallel plan
+    uint32_t pair_cap = 0, slot_cap = 0;
     ViewSet vs{};
     GaussParams P{};
     int64_t m = 0;      // instances of the last eager build
@@ -36,6 +41,19 @@ struct RenderState {
     uint32_t generation = 0;
 
     const uint32_t *sorted_tiles() const { return (const uint32_t *)(sorted_in_b ? inst_b_t.p : inst_a_t.p); }
+    ChunkPlan plan() const {
+        ChunkPlan cp;
+        cp.L = kChunkLen;
+        cp.n_chunks = (const uint32_t *)n_chunks.p;
+        cp.chunk_base = (const uint32_t *)chunk_base.p;
+        cp.part_base = (const uint32_t *)part_base.p;
+        cp.pair_tile = (const uint32_t *)pair_tile.p;
+        cp.n_pairs = (const uint32_t *)counters.p + 4;
+        cp.part = (float *)part.p;
+        cp.pair_cap = pair_cap;
+        cp.slot_cap = slot_cap;
+        return cp;
+    }
     const uint32_t *sorted_vals() const { return (const uint32_t *)(sorted_in_b ? inst_b_v.p : inst_a_v.p); }
 };
 
@@ -149,7 +167,8 @@ void release(lvigs_ctx *ctx, DevBuf &b) {
 
 void release_state(lvigs_ctx *ctx, RenderState &s) {
     DevBuf *all[] = {&s.recs, &s.tiles, &s.zbits, &s.rects, &s.inst_a_t, &s.inst_a_v, &s.inst_b_t,
-                     &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters};
+                     &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters,
+                     &s.n_chunks, &s.chunk_base, &s.n_slots, &s.part_base, &s.pair_tile, &s.part};
     for (DevBuf *b : all) release(ctx, *b);
     s.valid = false;
     s.m_cap = 0;
@@ -262,6 +281,20 @@ int key_bits(uint32_t total_tiles) {
     return b;
 }
 
+// Capacities of the list-parallel plan for m_cap instances: at most
+// tiles + m_cap / L pairs, and a multi-chunk tile of n > L entries owns at most
+// 2 n / L slots.
+lvigs_status ensure_plan(lvigs_ctx *ctx, RenderState &st) {
+    const uint64_t pairs = (uint64_t)st.vs.total_tiles + (uint64_t)st.m_cap / kChunkLen + 1;
+    const uint64_t slots = 2 * ((uint64_t)st.m_cap / kChunkLen) + 1;
+    if (pairs > 0xffffffffull || slots > 0xffffffffull) return fail(ctx, LVIGS_ERR_CAPACITY, "plan too large");
+    LV_TRY(ensure(ctx, st.pair_tile, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.part, (size_t)slots * chunk_slot_bytes(st.vs.tile_w, st.vs.tile_h)));
+    st.pair_cap = (uint32_t)pairs;
+    st.slot_cap = (uint32_t)slots;
+    return LVIGS_OK;
+}
+
 // a1-a4 for the views of `st`: preprocess, compact, depth sort, scan,
 // emit, tile sort, ranges.  In eager mode the call waits once to learn the
 // instance count and grows the instance buffers; otherwise it relies on
@@ -273,14 +306,19 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     LV_TRY(ensure(ctx, st.tiles, (size_t)VN * 4));
     LV_TRY(ensure(ctx, st.zbits, (size_t)VN * 4));
     LV_TRY(ensure(ctx, st.rects, (size_t)VN * 8));
-    LV_TRY(ensure(ctx, st.counters, 16));
+    LV_TRY(ensure(ctx, st.counters, 32));
     LV_TRY(ensure(ctx, st.ranges, (size_t)st.vs.total_tiles * sizeof(uint2)));
+    LV_TRY(ensure(ctx, st.n_chunks, (size_t)st.vs.total_tiles * 4));
+    LV_TRY(ensure(ctx, st.chunk_base, (size_t)st.vs.total_tiles * 4));
+    LV_TRY(ensure(ctx, st.n_slots, (size_t)st.vs.total_tiles * 4));
+    LV_TRY(ensure(ctx, st.part_base, (size_t)st.vs.total_tiles * 4));
     LV_TRY(ensure(ctx, ctx->pos, (size_t)VN * 4));
     LV_TRY(ensure(ctx, ctx->ck, (size_t)VN * 4));
     LV_TRY(ensure(ctx, ctx->cv, (size_t)VN * 4));
     LV_TRY(ensure(ctx, ctx->ck2, (size_t)VN * 4));
     LV_TRY(ensure(ctx, ctx->cv2, (size_t)VN * 4));
-    LV_TRY(ensure(ctx, ctx->scan_tmp, scan_tmp_words(VN) * 4));
+    const int64_t scan_n = VN > (int64_t)st.vs.total_tiles ? VN : (int64_t)st.vs.total_tiles;
+    LV_TRY(ensure(ctx, ctx->scan_tmp, scan_tmp_words(scan_n) * 4));
     LV_TRY(ensure(ctx, ctx->radix_tmp, radix_tmp_words((int64_t)1 << 40) * 4));
     LV_TRY(ensure(ctx, ctx->status, 16));
     if (!eager) {
@@ -288,8 +326,10 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
         LV_TRY(ensure(ctx, st.inst_a_v, (size_t)st.m_cap * 4));
         LV_TRY(ensure(ctx, st.inst_b_t, (size_t)st.m_cap * 4));
         LV_TRY(ensure(ctx, st.inst_b_v, (size_t)st.m_cap * 4));
+        LV_TRY(ensure_plan(ctx, st));
     }
-    uint32_t *cnt = (uint32_t *)st.counters.p; // [0] visible, [1] instances, [2] clamped
+    // [0] visible, [1] instances, [2] clamped instances, [3] work queue, [4] pairs, [5] slots
+    uint32_t *cnt = (uint32_t *)st.counters.p;
     const ViewSet *vsd = (const ViewSet *)st.vs_dev.p;
 
     {
@@ -328,6 +368,7 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
         LV_TRY(ensure(ctx, st.inst_a_v, (size_t)st.m_cap * 4));
         LV_TRY(ensure(ctx, st.inst_b_t, (size_t)st.m_cap * 4));
         LV_TRY(ensure(ctx, st.inst_b_v, (size_t)st.m_cap * 4));
+        LV_TRY(ensure_plan(ctx, st));
     }
     {
         Phase ph(ctx, LVIGS_PHASE_EMIT, s);
@@ -344,6 +385,14 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     {
         Phase ph(ctx, LVIGS_PHASE_RANGES, s);
         launch_ranges(st.sorted_tiles(), cnt + 2, st.m_cap, (uint2 *)st.ranges.p, st.vs.total_tiles, s);
+        // list-parallel plan: chunks per tile, pair and slot numbering
+        launch_chunk_counts((const uint2 *)st.ranges.p, st.vs.total_tiles, kChunkLen, (uint32_t *)st.n_chunks.p,
+                            (uint32_t *)st.n_slots.p, s);
+        launch_scan((const uint32_t *)st.n_chunks.p, nullptr, 0, (uint32_t *)st.chunk_base.p, cnt + 4, nullptr,
+                    st.vs.total_tiles, (uint32_t *)ctx->scan_tmp.p, s);
+        launch_scan((const uint32_t *)st.n_slots.p, nullptr, 0, (uint32_t *)st.part_base.p, cnt + 5, nullptr,
+                    st.vs.total_tiles, (uint32_t *)ctx->scan_tmp.p, s);
+        launch_chunk_pairs(st.plan(), st.vs.total_tiles, (uint32_t *)ctx->status.p, s);
     }
     return LVIGS_OK;
 }
@@ -508,7 +557,8 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
-                             (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s, ctx->bm);
+                             (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(),
+                             (uint32_t *)st.counters.p + 3, s, ctx->bm);
     }
     LV_CUDA(cudaGetLastError());
     st.valid = true;
@@ -538,7 +588,8 @@ lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
         launch_composite_bwd(st->vs, (const ViewSet *)st->vs_dev.p, (const uint2 *)st->ranges.p, st->sorted_vals(),
                              (const GRec *)st->recs.p, vg, (const float *)st->final_T.p,
-                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, s, ctx->bm);
+                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, st->plan(),
+                             (uint32_t *)st->counters.p + 3, s, ctx->bm);
     }
     ParamGrads G{grads->d_means, grads->d_log_scales, grads->d_quats, grads->d_opacity_logits, grads->d_sh,
                  grads->accumulate};
@@ -786,7 +837,8 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
-                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, s, ctx->bm);
+                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
+                             s, ctx->bm);
     }
     // 4. a8: loss and its image gradients for every view
     {
@@ -806,7 +858,8 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
         launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
-                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, s, ctx->bm);
+                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p,
+                             st.plan(), (uint32_t *)st.counters.p + 3, s, ctx->bm);
     }
     ParamGrads G{gr->d_means, gr->d_log_scales, gr->d_quats, gr->d_opacity_logits, gr->d_sh, gr->accumulate};
     {

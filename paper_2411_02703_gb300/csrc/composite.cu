@@ -1,27 +1,41 @@
 // composite.cu -- front-to-back alpha compositing (a5) and its reverse (a6).
 //
-// Work unit: one warp per 8x8 block of pixels, two vertically adjacent pixels
-// per lane.  A CTA holds the (tile_w/8) x (tile_h/8) warps of one (view,
-// tile); every warp walks the tile's depth-sorted instance list on its own
-// (no block-wide barrier), so a warp whose pixels saturate early, or that few
-// Gaussians reach, never waits for its neighbours.
+// Work unit: one 8x8 block of pixels per warp, two vertically adjacent pixels
+// per lane.  The kernels are persistent: a GPU-filling grid of warps takes
+// work items from a global counter (one atomicAdd per item; no warp ever
+// waits on another).
 //
-// The list is consumed in batches of 32*BM instances.  Each lane gathers
-// records and tests them against the warp's 8x8 block using the conservative
-// box of the region where alpha can reach 1/255 (half-extents precomputed by
-// preprocessing); the hits are compacted into the warp's shared-memory slice
-// with a ballot, in list order.  Culled Gaussians would fail the 1/255 test at
-// every pixel of the block, so results are exactly those of walking the whole
-// list.  Per pixel (Eq. (3)-(6)): alpha = min(0.99, o exp(power)), skipped
-// below 1/255, and the pixel stops before a Gaussian that would take the
-// transmittance below 1e-4.
+// List-parallel compositing.  A tile's depth-sorted instance list is cut into
+// chunks of L entries; every (tile, chunk, 8x8 block) is an independent work
+// item, so the tens of thousands of Gaussians that pile up in a tile of a
+// coarse pyramid level are composited by many warps at once instead of one.
+//   phase 1  each item walks its chunk (Eq. (3)-(6)): alpha = min(0.99,
+//            o exp(power)), skipped below 1/255, stop before a Gaussian that
+//            would take the transmittance below 1e-4.  A one-chunk tile is
+//            final here.  For a longer list the walk starts from T = 1 and
+//            stores the chunk's local sums (colour, depth, T, last contributor,
+//            whether the local T hit the stop, which implies the global stop
+//            lies at or before that Gaussian).
+//   phase 2  per pixel the chunks are combined in order: C += T C_k,
+//            T *= T_k, until the chunk whose end would cross 1e-4; that one
+//            chunk is walked again from the true T to find the exact stop.
+//            The pass then stores, for each chunk, the transmittance at its end
+//            and the normalised sums of everything composited after it (all
+//            terms non-negative, so no cancellation), which is the state the
+//            backward walk of that chunk starts from.
+// Within a walk the list is consumed in batches of 32*BM: each lane gathers
+// records and tests them against the block with the conservative box of the
+// region where alpha can reach 1/255 (half-extents from preprocessing); the
+// hits are compacted into shared memory with a ballot, in list order.  Culled
+// Gaussians fail the 1/255 test at every pixel of the block, so results equal
+// those of walking the whole list.
 //
-// The backward pass walks the same list in reverse from the warp's last
+// The backward pass walks each chunk in reverse from the pixel's last
 // contributor, recovering the transmittance by division (T_i = T_{i+1} /
-// (1 - alpha_i)) so no per-Gaussian state is stored.  Each lane sums its two
+// (1 - alpha_i)); no per-Gaussian state is stored.  Each lane sums its two
 // pixels' ten screen-space gradient terms, the warp reduce-scatters the ten
-// sums with 12 shuffles, and the ten lanes that end with a total add it to
-// the Gaussian's gradient record with one atomic instruction.
+// sums with 12 shuffles, and the ten lanes that end with a total add it to the
+// Gaussian's gradient record with one atomic instruction.
 #include "lvigs_internal.cuh"
 
 namespace lvigs {
@@ -32,6 +46,8 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr int PB = 8;  // warp pixel block is PB x PB
 constexpr int PPT = 2; // pixels per lane (rows 2r, 2r+1 of the block)
+constexpr int kWarpsPerCta = 4;
+constexpr int kFields = 6; // per (pixel, chunk) slot
 
 // does the alpha box of record (a, b, c) meet the block [x0, x0+7] x [y0, y0+7]?
 __device__ __forceinline__ bool meets(const float4 a, const float4 b, const float4 c, float x0, float y0) {
@@ -42,72 +58,86 @@ __device__ __forceinline__ bool meets(const float4 a, const float4 b, const floa
 template <int TW, int TH>
 struct Geometry {
     static constexpr int WX = TW / PB, WY = TH / PB;
-    static constexpr int NW = WX * WY;
-    static constexpr int NT = NW * 32;
+    static constexpr int NB = WX * WY; // 8x8 blocks per tile
+    static constexpr int TPX = TW * TH;
     static_assert(TW % PB == 0 && TH % PB == 0, "tile is a whole number of 8x8 blocks");
 };
 
-template <int TW, int TH, int BM>
-__global__ void __launch_bounds__(Geometry<TW, TH>::NT)
-composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
-                     const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs,
-                     ViewImages out, float *__restrict__ final_T, int32_t *__restrict__ n_contrib) {
-    using Gm = Geometry<TW, TH>;
-    constexpr int B = 32 * BM;
-    __shared__ float4 s_a[Gm::NW][B], s_b[Gm::NW][B], s_c[Gm::NW][B];
-    __shared__ int s_pos[Gm::NW][B];
-    const uint32_t gt = blockIdx.x;
-    const int vi = view_of_tile(*vsp, gt);
-    const ViewDesc &V = vsp->v[vi];
-    const uint32_t lt = gt - V.tile_base;
-    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx0 = tx * TW + (warp % Gm::WX) * PB, by0 = ty * TH + (warp / Gm::WX) * PB;
-    const int px = bx0 + (lane & 7), py0 = by0 + (lane >> 3) * PPT;
-    const float fpx = (float)px, fx0 = (float)bx0, fy0 = (float)by0;
-    const uint2 rg = ranges[gt];
-    const uint32_t ltmask = (1u << lane) - 1u;
-    float4 *A = s_a[warp], *Bv = s_b[warp], *Cv = s_c[warp];
-    int *Pos = s_pos[warp];
-
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
-    int last[PPT];
-    bool done[PPT];
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        T[k] = 1.f;
-        C0[k] = C1[k] = C2[k] = D[k] = 0.f;
-        last[k] = 0;
-        done[k] = !(px < V.W && py0 + k < V.H);
+// Pixel coordinates of a lane in block `blk` of the tile with local index lt.
+template <int TW, int TH>
+struct BlockPix {
+    int px, py0; // image coordinates of the lane's pixels (px, py0) and (px, py0 + 1)
+    int lp0;     // tile-local index of the first pixel (the second is lp0 + TW)
+    float fx0, fy0;
+    __device__ __forceinline__ BlockPix(const ViewDesc &V, uint32_t lt, int blk, int lane) {
+        using Gm = Geometry<TW, TH>;
+        const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
+        const int lx = (blk % Gm::WX) * PB + (lane & 7), ly = (blk / Gm::WX) * PB + (lane >> 3) * PPT;
+        px = tx * TW + lx;
+        py0 = ty * TH + ly;
+        lp0 = ly * TW + lx;
+        fx0 = (float)(tx * TW + (blk % Gm::WX) * PB);
+        fy0 = (float)(ty * TH + (blk / Gm::WX) * PB);
     }
-    bool tdone = done[0] && done[1];
-    for (uint32_t base = rg.x; base < rg.y; base += B) {
-        if (__all_sync(0xffffffffu, tdone)) break;
-        // gather and compact the Gaussians whose alpha box meets this block
-        int n = 0;
+};
+
+struct Smem {
+    float4 *A, *B, *C;
+    int *Pos;
+    uint32_t *Idx;
+};
+
+// Gather list entries [base, min(base + 32*BM, hi)) and compact the ones whose
+// alpha box meets the block into shared memory (list order).  Returns the count.
+template <int BM, bool WITH_IDX>
+__device__ __forceinline__ int gather_cull(const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs,
+                                           uint32_t rg_x, uint32_t base, uint32_t hi, float fx0, float fy0,
+                                           const Smem &sm, int lane) {
+    const uint32_t ltmask = (1u << lane) - 1u;
+    int n = 0;
 #pragma unroll
-        for (int q = 0; q < BM; ++q) {
-            const uint32_t i = base + q * 32 + lane;
-            GRec r;
-            bool hit = false;
-            if (i < rg.y) {
-                r = recs[inst_vals[i]];
-                hit = meets(r.a, r.b, r.c, fx0, fy0);
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int slot = n + __popc(m & ltmask);
-                A[slot] = r.a;
-                Bv[slot] = r.b;
-                Cv[slot] = r.c;
-                Pos[slot] = (int)(i - rg.x);
-            }
-            n += __popc(m);
+    for (int q = 0; q < BM; ++q) {
+        const uint32_t i = base + q * 32 + lane;
+        GRec r;
+        uint32_t idx = 0;
+        bool hit = false;
+        if (i < hi) {
+            idx = inst_vals[i];
+            r = recs[idx];
+            hit = meets(r.a, r.b, r.c, fx0, fy0);
         }
-        __syncwarp();
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int slot = n + __popc(m & ltmask);
+            sm.A[slot] = r.a;
+            sm.B[slot] = r.b;
+            sm.C[slot] = r.c;
+            sm.Pos[slot] = (int)(i - rg_x);
+            if (WITH_IDX) sm.Idx[slot] = idx;
+        }
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
+// Front-to-back walk of list entries [lo, hi) for the lane's pixels, from the
+// state passed in.  Pixels with done[k] set are left alone; stopped[k] is set
+// when the pixel stops (the transmittance test) inside this walk.
+template <int BM>
+__device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs,
+                                         uint32_t rg_x, uint32_t lo, uint32_t hi, float fpx, int py0, float fx0,
+                                         float fy0, const Smem &sm, int lane, float T[PPT], float C0[PPT],
+                                         float C1[PPT], float C2[PPT], float D[PPT], int last[PPT], bool done[PPT],
+                                         bool stopped[PPT]) {
+    constexpr int B = 32 * BM;
+    bool tdone = done[0] && done[1];
+    for (uint32_t base = lo; base < hi; base += B) {
+        if (__all_sync(0xffffffffu, tdone)) break;
+        const int n = gather_cull<BM, false>(inst_vals, recs, rg_x, base, hi, fx0, fy0, sm, lane);
         for (int q = 0; q < n && !tdone; ++q) {
-            const float4 a = A[q];
-            const float4 b = Bv[q];
+            const float4 a = sm.A[q];
+            const float4 b = sm.B[q];
             const float dx = a.x - fpx;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -120,34 +150,252 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
                     done[k] = true;
+                    stopped[k] = true;
                     continue;
                 }
-                const float4 c = Cv[q];
+                const float4 c = sm.C[q];
                 const float w = alpha * T[k];
                 C0[k] = fmaf(c.x, w, C0[k]);
                 C1[k] = fmaf(c.y, w, C1[k]);
                 C2[k] = fmaf(c.z, w, C2[k]);
                 D[k] = fmaf(b.z, w, D[k]);
                 T[k] = Tn;
-                last[k] = Pos[q] + 1;
+                last[k] = sm.Pos[q] + 1;
             }
             tdone = done[0] && done[1];
         }
         __syncwarp();
     }
-    const size_t HW = (size_t)V.W * V.H;
+}
+
+__device__ __forceinline__ void write_final(const ViewDesc &V, const ViewImages &out, int vi, float *final_T,
+                                            int32_t *n_contrib, int px, int py, float T, float C0, float C1,
+                                            float C2, float D, int last) {
+    if (px < V.W && py < V.H) {
+        const size_t HW = (size_t)V.W * V.H;
+        const size_t p = (size_t)py * V.W + px;
+        out.rgb[vi][p] = C0;
+        out.rgb[vi][HW + p] = C1;
+        out.rgb[vi][2 * HW + p] = C2;
+        out.depth[vi][p] = D;
+        out.alpha[vi][p] = 1.f - T;
+        final_T[V.pix_base + p] = T;
+        n_contrib[V.pix_base + p] = last;
+    }
+}
+
+__device__ __forceinline__ float *slot_field(const ChunkPlan &cp, uint32_t slot, int field, int tpx) {
+    return cp.part + ((size_t)slot * kFields + field) * (size_t)tpx;
+}
+
+__device__ __forceinline__ uint32_t take_item(uint32_t *queue, int lane) {
+    uint32_t item = 0;
+    if (lane == 0) item = atomicAdd(queue, 1u);
+    return __shfl_sync(0xffffffffu, item, 0);
+}
+
+// Phase 1: (tile, chunk, block) items.
+template <int TW, int TH, int BM>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
+                     const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
+                     float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
+                     uint32_t *__restrict__ queue) {
+    using Gm = Geometry<TW, TH>;
+    constexpr int B = 32 * BM;
+    __shared__ float4 sA[kWarpsPerCta][B], sB[kWarpsPerCta][B], sC[kWarpsPerCta][B];
+    __shared__ int sP[kWarpsPerCta][B];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
+    const uint32_t n_items = min(*cp.n_pairs, cp.pair_cap) * Gm::NB;
+    for (;;) {
+        const uint32_t item = take_item(queue, lane);
+        if (item >= n_items) break;
+        const uint32_t pair = item / Gm::NB;
+        const int blk = (int)(item % Gm::NB);
+        const uint32_t gt = cp.pair_tile[pair];
+        if (gt >= vsp->total_tiles) continue; // never written (capacity overflow, latched)
+        const uint32_t nch = cp.n_chunks[gt];
+        const uint32_t k = pair - cp.chunk_base[gt];
+        if (k >= nch) continue;
+        const int vi = view_of_tile(*vsp, gt);
+        const ViewDesc &V = vsp->v[vi];
+        const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+        const uint2 rg = ranges[gt];
+        const uint32_t lo = rg.x + k * (uint32_t)cp.L;
+        const uint32_t hi = min(rg.y, lo + (uint32_t)cp.L);
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+        int last[PPT];
+        bool done[PPT], stopped[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int py = py0 + k;
-        if (px < V.W && py < V.H) {
-            const size_t p = (size_t)py * V.W + px;
-            out.rgb[vi][p] = C0[k];
-            out.rgb[vi][HW + p] = C1[k];
-            out.rgb[vi][2 * HW + p] = C2[k];
-            out.depth[vi][p] = D[k];
-            out.alpha[vi][p] = 1.f - T[k];
-            final_T[V.pix_base + p] = T[k];
-            n_contrib[V.pix_base + p] = last[k];
+        for (int j = 0; j < PPT; ++j) {
+            T[j] = 1.f;
+            C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+            last[j] = 0;
+            done[j] = !(bp.px < V.W && bp.py0 + j < V.H);
+            stopped[j] = false;
+        }
+        fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2,
+                     D, last, done, stopped);
+        if (nch <= 1) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+                write_final(V, out, vi, final_T, n_contrib, bp.px, bp.py0 + j, T[j], C0[j], C1[j], C2[j], D[j],
+                            last[j]);
+        } else {
+            const uint32_t slot = cp.part_base[gt] + k;
+            if (slot >= cp.slot_cap) continue; // capacity overflow is latched by the planner
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int lp = bp.lp0 + j * TW;
+                slot_field(cp, slot, 0, Gm::TPX)[lp] = C0[j];
+                slot_field(cp, slot, 1, Gm::TPX)[lp] = C1[j];
+                slot_field(cp, slot, 2, Gm::TPX)[lp] = C2[j];
+                slot_field(cp, slot, 3, Gm::TPX)[lp] = D[j];
+                slot_field(cp, slot, 4, Gm::TPX)[lp] = T[j];
+                slot_field(cp, slot, 5, Gm::TPX)[lp] =
+                    __int_as_float(last[j] | (stopped[j] ? (int)0x80000000 : 0));
+            }
+        }
+    }
+}
+
+// Phase 2: combine the chunks of multi-chunk tiles, one (tile, block) per warp.
+template <int TW, int TH, int BM>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+composite_combine_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
+                         const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
+                         float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
+                         uint32_t total_tiles) {
+    using Gm = Geometry<TW, TH>;
+    constexpr int B = 32 * BM;
+    constexpr int TPX = Gm::TPX;
+    __shared__ float4 sA[kWarpsPerCta][B], sB[kWarpsPerCta][B], sC[kWarpsPerCta][B];
+    __shared__ int sP[kWarpsPerCta][B];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t item = blockIdx.x * kWarpsPerCta + w;
+    if (item >= total_tiles * Gm::NB) return;
+    const uint32_t gt = item / Gm::NB;
+    const int blk = (int)(item % Gm::NB);
+    const uint32_t nch = cp.n_chunks[gt];
+    if (nch <= 1) return;
+    const uint32_t s0 = cp.part_base[gt];
+    if (s0 + nch > cp.slot_cap) return; // capacity overflow is latched by the planner
+    const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
+    const int vi = view_of_tile(*vsp, gt);
+    const ViewDesc &V = vsp->v[vi];
+    const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+    const uint2 rg = ranges[gt];
+
+    // pass 1: running combination up to the chunk where the pixel stops
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT];
+    int last[PPT], stop[PPT];
+    bool inside[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        T[j] = 1.f;
+        C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+        last[j] = 0;
+        stop[j] = -1;
+        Tin[j] = 1.f;
+        inside[j] = bp.px < V.W && bp.py0 + j < V.H;
+    }
+    for (uint32_t k = 0; k < nch; ++k) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            if (!inside[j] || stop[j] >= 0) continue;
+            const int lp = bp.lp0 + j * TW;
+            const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
+            const int lk = __float_as_int(slot_field(cp, s0 + k, 5, TPX)[lp]);
+            const float Tn = __fmul_rn(T[j], Tk);
+            if ((lk & (int)0x80000000) || Tn < kTMin) {
+                stop[j] = (int)k;
+                Tin[j] = T[j];
+                continue;
+            }
+            C0[j] = fmaf(T[j], slot_field(cp, s0 + k, 0, TPX)[lp], C0[j]);
+            C1[j] = fmaf(T[j], slot_field(cp, s0 + k, 1, TPX)[lp], C1[j]);
+            C2[j] = fmaf(T[j], slot_field(cp, s0 + k, 2, TPX)[lp], C2[j]);
+            D[j] = fmaf(T[j], slot_field(cp, s0 + k, 3, TPX)[lp], D[j]);
+            T[j] = Tn;
+            if (lk) last[j] = lk;
+        }
+    }
+    // pass 2: exact walk of the stop chunk from the true transmittance
+    float rC0[PPT], rC1[PPT], rC2[PPT], rD[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        rC0[j] = C0[j];
+        rC1[j] = C1[j];
+        rC2[j] = C2[j];
+        rD[j] = D[j];
+    }
+    for (uint32_t k = 0; k < nch; ++k) {
+        const bool need = (stop[0] == (int)k) || (stop[1] == (int)k);
+        if (!__any_sync(0xffffffffu, need)) continue;
+        bool done[PPT], stopped[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            done[j] = stop[j] != (int)k;
+            stopped[j] = false;
+        }
+        const uint32_t lo = rg.x + k * (uint32_t)cp.L;
+        const uint32_t hi = min(rg.y, lo + (uint32_t)cp.L);
+        fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2, D,
+                     last, done, stopped);
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j)
+        write_final(V, out, vi, final_T, n_contrib, bp.px, bp.py0 + j, T[j], C0[j], C1[j], C2[j], D[j], last[j]);
+
+    // pass 3: per chunk, the transmittance at its end and the normalised sums
+    // of everything composited after it (the backward walk's starting state).
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        if (!inside[j]) continue;
+        const int lp = bp.lp0 + j * TW;
+        // 3a: each slot becomes (contribution of the chunk to C, D, V; T at its end)
+        float t = 1.f;
+        const uint32_t top = stop[j] >= 0 ? (uint32_t)stop[j] : nch - 1;
+        for (uint32_t k = 0; k <= top; ++k) {
+            float g0, g1, g2, gd, ga, tend;
+            if ((int)k == stop[j]) {
+                g0 = C0[j] - rC0[j];
+                g1 = C1[j] - rC1[j];
+                g2 = C2[j] - rC2[j];
+                gd = D[j] - rD[j];
+                ga = Tin[j] - T[j];
+                tend = T[j];
+            } else {
+                const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
+                g0 = t * slot_field(cp, s0 + k, 0, TPX)[lp];
+                g1 = t * slot_field(cp, s0 + k, 1, TPX)[lp];
+                g2 = t * slot_field(cp, s0 + k, 2, TPX)[lp];
+                gd = t * slot_field(cp, s0 + k, 3, TPX)[lp];
+                tend = __fmul_rn(t, Tk);
+                ga = t - tend;
+            }
+            slot_field(cp, s0 + k, 0, TPX)[lp] = g0;
+            slot_field(cp, s0 + k, 1, TPX)[lp] = g1;
+            slot_field(cp, s0 + k, 2, TPX)[lp] = g2;
+            slot_field(cp, s0 + k, 3, TPX)[lp] = gd;
+            slot_field(cp, s0 + k, 4, TPX)[lp] = ga;
+            slot_field(cp, s0 + k, 5, TPX)[lp] = tend;
+            t = tend;
+        }
+        // 3b: suffix sums, normalised by the transmittance at each chunk's end
+        float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = (int)top; k >= 0; --k) {
+            float g[5];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) g[f] = slot_field(cp, s0 + k, f, TPX)[lp];
+            const float tend = slot_field(cp, s0 + k, 5, TPX)[lp];
+            const float inv = tend > 0.f ? 1.f / tend : 0.f;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                slot_field(cp, s0 + k, f, TPX)[lp] = s[f] * inv;
+                s[f] += g[f];
+            }
         }
     }
 }
@@ -192,193 +440,262 @@ __device__ __forceinline__ float reduce_scatter10(const float v[10], int lane, i
 }
 
 // float offset in GGrad of reduced value index: du dv dA dB dC dop dr dg db dz
-__device__ __forceinline__ int grad_offset(int idx) {
-    return idx < 6 ? idx : (idx < 9 ? idx + 2 : 6);
-}
+__device__ __forceinline__ int grad_offset(int idx) { return idx < 6 ? idx : (idx < 9 ? idx + 2 : 6); }
 
 template <int TW, int TH, int BM>
-__global__ void __launch_bounds__(Geometry<TW, TH>::NT)
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
 composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
-                     const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs,
-                     ViewGrads G, const float *__restrict__ final_T,
-                     const int32_t *__restrict__ n_contrib, GGrad *__restrict__ g2d) {
+                     const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewGrads G,
+                     const float *__restrict__ final_T, const int32_t *__restrict__ n_contrib,
+                     GGrad *__restrict__ g2d, ChunkPlan cp, uint32_t *__restrict__ queue) {
     using Gm = Geometry<TW, TH>;
     constexpr int B = 32 * BM;
     constexpr int NACC = 10;
-    __shared__ float4 s_a[Gm::NW][B], s_b[Gm::NW][B], s_c[Gm::NW][B];
-    __shared__ int s_pos[Gm::NW][B];
-    __shared__ uint32_t s_idx[Gm::NW][B];
-    const uint32_t gt = blockIdx.x;
-    const int vi = view_of_tile(*vsp, gt);
-    const ViewDesc &V = vsp->v[vi];
-    const uint32_t lt = gt - V.tile_base;
-    const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx0 = tx * TW + (warp % Gm::WX) * PB, by0 = ty * TH + (warp / Gm::WX) * PB;
-    const int px = bx0 + (lane & 7), py0 = by0 + (lane >> 3) * PPT;
-    const float fpx = (float)px, fx0 = (float)bx0, fy0 = (float)by0;
-    const uint2 rg = ranges[gt];
-    const uint32_t ltmask = (1u << lane) - 1u;
-    const size_t HW = (size_t)V.W * V.H;
-    float4 *A = s_a[warp], *Bv = s_b[warp], *Cv = s_c[warp];
-    int *Pos = s_pos[warp];
-    uint32_t *Idx = s_idx[warp];
+    __shared__ float4 sA[kWarpsPerCta][B], sB[kWarpsPerCta][B], sC[kWarpsPerCta][B];
+    __shared__ int sP[kWarpsPerCta][B];
+    __shared__ uint32_t sI[kWarpsPerCta][B];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Smem sm{sA[w], sB[w], sC[w], sP[w], sI[w]};
+    const uint32_t n_items = min(*cp.n_pairs, cp.pair_cap) * Gm::NB;
+    for (;;) {
+        const uint32_t item = take_item(queue, lane);
+        if (item >= n_items) break;
+        const uint32_t pair = item / Gm::NB;
+        const int blk = (int)(item % Gm::NB);
+        const uint32_t gt = cp.pair_tile[pair];
+        if (gt >= vsp->total_tiles) continue; // never written (capacity overflow, latched)
+        const uint32_t nch = cp.n_chunks[gt];
+        const uint32_t k = pair - cp.chunk_base[gt];
+        if (k >= nch || (nch > 1 && cp.part_base[gt] + k >= cp.slot_cap)) continue;
+        const int vi = view_of_tile(*vsp, gt);
+        const ViewDesc &V = vsp->v[vi];
+        const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+        const uint2 rg = ranges[gt];
+        const size_t HW = (size_t)V.W * V.H;
+        const float fpx = (float)bp.px;
 
-    float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT];
-    float S0[PPT], S1[PPT], S2[PPT], SD[PPT], SA[PPT];
-    int last[PPT];
+        float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT];
+        float S0[PPT], S1[PPT], S2[PPT], SD[PPT], SA[PPT];
+        int last[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int py = py0 + k;
-        T[k] = 1.f;
-        gC0[k] = gC1[k] = gC2[k] = gD[k] = gA[k] = 0.f;
-        S0[k] = S1[k] = S2[k] = SD[k] = SA[k] = 0.f;
-        last[k] = 0;
-        if (px < V.W && py < V.H) {
-            const size_t p = (size_t)py * V.W + px;
-            T[k] = final_T[V.pix_base + p];
-            last[k] = n_contrib[V.pix_base + p];
-            gC0[k] = G.d_rgb[vi][p];
-            gC1[k] = G.d_rgb[vi][HW + p];
-            gC2[k] = G.d_rgb[vi][2 * HW + p];
-            gD[k] = G.d_depth[vi] ? G.d_depth[vi][p] : 0.f;
-            gA[k] = G.d_alpha[vi] ? G.d_alpha[vi][p] : 0.f;
+        for (int j = 0; j < PPT; ++j) {
+            const int py = bp.py0 + j;
+            T[j] = 1.f;
+            gC0[j] = gC1[j] = gC2[j] = gD[j] = gA[j] = 0.f;
+            S0[j] = S1[j] = S2[j] = SD[j] = SA[j] = 0.f;
+            last[j] = 0;
+            if (bp.px < V.W && py < V.H) {
+                const size_t p = (size_t)py * V.W + bp.px;
+                last[j] = n_contrib[V.pix_base + p];
+                if (nch <= 1) {
+                    T[j] = final_T[V.pix_base + p];
+                } else if (k * (uint32_t)cp.L < (uint32_t)last[j]) {
+                    const uint32_t slot = cp.part_base[gt] + k;
+                    const int lp = bp.lp0 + j * TW;
+                    S0[j] = slot_field(cp, slot, 0, Gm::TPX)[lp];
+                    S1[j] = slot_field(cp, slot, 1, Gm::TPX)[lp];
+                    S2[j] = slot_field(cp, slot, 2, Gm::TPX)[lp];
+                    SD[j] = slot_field(cp, slot, 3, Gm::TPX)[lp];
+                    SA[j] = slot_field(cp, slot, 4, Gm::TPX)[lp];
+                    T[j] = slot_field(cp, slot, 5, Gm::TPX)[lp];
+                }
+                gC0[j] = G.d_rgb[vi][p];
+                gC1[j] = G.d_rgb[vi][HW + p];
+                gC2[j] = G.d_rgb[vi][2 * HW + p];
+                gD[j] = G.d_depth[vi] ? G.d_depth[vi][p] : 0.f;
+                gA[j] = G.d_alpha[vi] ? G.d_alpha[vi][p] : 0.f;
+            }
         }
-    }
-    const int warp_last = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
-    const uint32_t end = rg.x + (uint32_t)warp_last;
+        const int warp_last = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
+        const uint32_t lo_chunk = rg.x + k * (uint32_t)cp.L;
+        const uint32_t end = min(min(rg.y, lo_chunk + (uint32_t)cp.L), rg.x + (uint32_t)warp_last);
 
-    for (uint32_t hi = end; hi > rg.x;) {
-        const uint32_t lo = hi - rg.x > (uint32_t)B ? hi - B : rg.x;
-        int n = 0;
+        for (uint32_t hi = end; hi > lo_chunk;) {
+            const uint32_t lo = hi - lo_chunk > (uint32_t)B ? hi - B : lo_chunk;
+            const int n = gather_cull<BM, true>(inst_vals, recs, rg.x, lo, hi, bp.fx0, bp.fy0, sm, lane);
+            for (int q = n - 1; q >= 0; --q) {
+                const float4 a = sm.A[q];
+                const float4 b = sm.B[q];
+                const float4 c = sm.C[q];
+                const int pos = sm.Pos[q];
+                const float dx = a.x - fpx;
+                float v[NACC];
 #pragma unroll
-        for (int q = 0; q < BM; ++q) {
-            const uint32_t i = lo + q * 32 + lane;
-            GRec r;
-            uint32_t idx = 0;
-            bool hit = false;
-            if (i < hi) {
-                idx = inst_vals[i];
-                r = recs[idx];
-                hit = meets(r.a, r.b, r.c, fx0, fy0);
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-                const int slot = n + __popc(m & ltmask);
-                A[slot] = r.a;
-                Bv[slot] = r.b;
-                Cv[slot] = r.c;
-                Pos[slot] = (int)(i - rg.x);
-                Idx[slot] = idx;
-            }
-            n += __popc(m);
-        }
-        __syncwarp();
-        for (int q = n - 1; q >= 0; --q) {
-            const float4 a = A[q];
-            const float4 b = Bv[q];
-            const float4 c = Cv[q];
-            const int pos = Pos[q];
-            const float dx = a.x - fpx;
-            float v[NACC];
+                for (int m = 0; m < NACC; ++m) v[m] = 0.f;
+                bool any = false;
 #pragma unroll
-            for (int m = 0; m < NACC; ++m) v[m] = 0.f;
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                if (pos >= last[k]) continue;
-                const float dy = a.y - (float)(py0 + k);
-                const float power = gauss_power(a.z, a.w, b.x, dx, dy);
-                if (power > 0.f) continue;
-                const float G_ = __expf(power);
-                const float oG = __fmul_rn(b.y, G_);
-                const float alpha = fminf(kAlphaMax, oG);
-                if (alpha < kAlphaMin) continue;
-                any = true;
-                const float one_m = 1.f - alpha;
-                T[k] = __fdividef(T[k], one_m);
-                const float w = alpha * T[k];
-                const float dLda = T[k] * ((c.x - S0[k]) * gC0[k] + (c.y - S1[k]) * gC1[k] +
-                                           (c.z - S2[k]) * gC2[k] + (b.z - SD[k]) * gD[k] + (1.f - SA[k]) * gA[k]);
-                S0[k] = fmaf(alpha, c.x - S0[k], S0[k]);
-                S1[k] = fmaf(alpha, c.y - S1[k], S1[k]);
-                S2[k] = fmaf(alpha, c.z - S2[k], S2[k]);
-                SD[k] = fmaf(alpha, b.z - SD[k], SD[k]);
-                SA[k] = fmaf(alpha, 1.f - SA[k], SA[k]);
-                v[6] = fmaf(w, gC0[k], v[6]);
-                v[7] = fmaf(w, gC1[k], v[7]);
-                v[8] = fmaf(w, gC2[k], v[8]);
-                v[9] = fmaf(w, gD[k], v[9]);
-                if (oG < kAlphaMax) {
-                    const float dpow = dLda * alpha;
-                    v[5] = fmaf(dLda, G_, v[5]);
-                    v[0] -= dpow * (a.z * dx + a.w * dy);
-                    v[1] -= dpow * (b.x * dy + a.w * dx);
-                    v[2] -= 0.5f * dpow * dx * dx;
-                    v[3] -= dpow * dx * dy;
-                    v[4] -= 0.5f * dpow * dy * dy;
+                for (int j = 0; j < PPT; ++j) {
+                    if (pos >= last[j]) continue;
+                    const float dy = a.y - (float)(bp.py0 + j);
+                    const float power = gauss_power(a.z, a.w, b.x, dx, dy);
+                    if (power > 0.f) continue;
+                    const float G_ = __expf(power);
+                    const float oG = __fmul_rn(b.y, G_);
+                    const float alpha = fminf(kAlphaMax, oG);
+                    if (alpha < kAlphaMin) continue;
+                    any = true;
+                    const float one_m = 1.f - alpha;
+                    T[j] = __fdividef(T[j], one_m);
+                    const float wgt = alpha * T[j];
+                    const float dLda = T[j] * ((c.x - S0[j]) * gC0[j] + (c.y - S1[j]) * gC1[j] +
+                                               (c.z - S2[j]) * gC2[j] + (b.z - SD[j]) * gD[j] + (1.f - SA[j]) * gA[j]);
+                    S0[j] = fmaf(alpha, c.x - S0[j], S0[j]);
+                    S1[j] = fmaf(alpha, c.y - S1[j], S1[j]);
+                    S2[j] = fmaf(alpha, c.z - S2[j], S2[j]);
+                    SD[j] = fmaf(alpha, b.z - SD[j], SD[j]);
+                    SA[j] = fmaf(alpha, 1.f - SA[j], SA[j]);
+                    v[6] = fmaf(wgt, gC0[j], v[6]);
+                    v[7] = fmaf(wgt, gC1[j], v[7]);
+                    v[8] = fmaf(wgt, gC2[j], v[8]);
+                    v[9] = fmaf(wgt, gD[j], v[9]);
+                    if (oG < kAlphaMax) {
+                        const float dpow = dLda * alpha;
+                        v[5] = fmaf(dLda, G_, v[5]);
+                        v[0] -= dpow * (a.z * dx + a.w * dy);
+                        v[1] -= dpow * (b.x * dy + a.w * dx);
+                        v[2] -= 0.5f * dpow * dx * dx;
+                        v[3] -= dpow * dx * dy;
+                        v[4] -= 0.5f * dpow * dy * dy;
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    int vidx;
+                    bool valid;
+                    const float tot = reduce_scatter10(v, lane, vidx, valid);
+                    if (valid && tot != 0.f) atomicAdd((float *)(g2d + sm.Idx[q]) + grad_offset(vidx), tot);
                 }
             }
-            if (__any_sync(0xffffffffu, any)) {
-                int vidx;
-                bool valid;
-                const float tot = reduce_scatter10(v, lane, vidx, valid);
-                if (valid && tot != 0.f) atomicAdd((float *)(g2d + Idx[q]) + grad_offset(vidx), tot);
-            }
+            __syncwarp();
+            hi = lo;
         }
-        __syncwarp();
-        hi = lo;
     }
+}
+
+// Chunk plan: chunks per tile, and for multi-chunk tiles the number of slots.
+__global__ void chunk_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L,
+                                   uint32_t *__restrict__ n_chunks, uint32_t *__restrict__ n_slots) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        const uint32_t c = len > L ? (len + L - 1) / L : 1u;
+        n_chunks[t] = c;
+        n_slots[t] = c > 1 ? c : 0u;
+    }
+}
+
+__global__ void chunk_pairs_kernel(const uint32_t *__restrict__ n_chunks, const uint32_t *__restrict__ chunk_base,
+                                   const uint32_t *__restrict__ part_base, uint32_t n_tiles,
+                                   uint32_t *__restrict__ pair_tile, uint32_t pair_cap, uint32_t slot_cap,
+                                   uint32_t *status) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+        const uint32_t c = n_chunks[t], b = chunk_base[t];
+        if (c > 1 && part_base[t] + c > slot_cap) atomicOr(status, kStatusCapacity);
+        if (b + c > pair_cap) {
+            atomicOr(status, kStatusCapacity);
+            continue;
+        }
+        for (uint32_t k = 0; k < c; ++k) pair_tile[b + k] = t;
+    }
+}
+
+template <typename K>
+unsigned persistent_grid(K kernel, uint64_t max_items) {
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerCta * 32, 0);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t want = (uint64_t)sms * per_sm;
+    const uint64_t need = (max_items + kWarpsPerCta - 1) / kWarpsPerCta;
+    return (unsigned)(want < need ? want : (need > 0 ? need : 1));
 }
 
 template <int TW, int TH, int BM>
 void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
-                const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, cudaStream_t s) {
-    composite_fwd_kernel<TW, TH, BM><<<vs.total_tiles, Geometry<TW, TH>::NT, 0, s>>>(vsd, ranges, inst_vals, recs, out,
-                                                                                   final_T, n_contrib);
+                const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
+                uint32_t *queue, cudaStream_t s) {
+    using Gm = Geometry<TW, TH>;
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    const uint64_t max_items = (uint64_t)cp.pair_cap * Gm::NB;
+    composite_fwd_kernel<TW, TH, BM><<<persistent_grid(composite_fwd_kernel<TW, TH, BM>, max_items),
+                                       kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
+                                                                  n_contrib, cp, queue);
+    const uint64_t tw = (uint64_t)vs.total_tiles * Gm::NB;
+    composite_combine_kernel<TW, TH, BM><<<(unsigned)((tw + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32,
+                                           0, s>>>(vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp,
+                                                   vs.total_tiles);
 }
 
 template <int TW, int TH, int BM>
-void bwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
-                const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
-                GGrad *g2d, cudaStream_t s) {
-    composite_bwd_kernel<TW, TH, BM><<<vs.total_tiles, Geometry<TW, TH>::NT, 0, s>>>(vsd, ranges, inst_vals, recs, g,
-                                                                                   final_T, n_contrib, g2d);
+void bwd_launch(const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals, const GRec *recs,
+                const ViewGrads &g, const float *final_T, const int32_t *n_contrib, GGrad *g2d, const ChunkPlan &cp,
+                uint32_t *queue, cudaStream_t s) {
+    using Gm = Geometry<TW, TH>;
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    const uint64_t max_items = (uint64_t)cp.pair_cap * Gm::NB;
+    composite_bwd_kernel<TW, TH, BM><<<persistent_grid(composite_bwd_kernel<TW, TH, BM>, max_items),
+                                       kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, g, final_T,
+                                                                  n_contrib, g2d, cp, queue);
 }
 
 template <int BM>
 void fwd_dispatch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
-                  const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, cudaStream_t s) {
-    if (vs.tile_w == 16 && vs.tile_h == 16) fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, s);
-    else if (vs.tile_w == 8 && vs.tile_h == 8) fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, s);
-    else if (vs.tile_w == 32 && vs.tile_h == 16) fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, s);
+                  const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
+                  uint32_t *queue, cudaStream_t s) {
+    if (vs.tile_w == 16 && vs.tile_h == 16)
+        fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+    else if (vs.tile_w == 8 && vs.tile_h == 8)
+        fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+    else if (vs.tile_w == 32 && vs.tile_h == 16)
+        fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
 }
 
 template <int BM>
 void bwd_dispatch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                   const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib, GGrad *g2d,
-                  cudaStream_t s) {
-    if (vs.tile_w == 16 && vs.tile_h == 16) bwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, s);
-    else if (vs.tile_w == 8 && vs.tile_h == 8) bwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, s);
-    else if (vs.tile_w == 32 && vs.tile_h == 16) bwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, s);
+                  const ChunkPlan &cp, uint32_t *queue, cudaStream_t s) {
+    if (vs.tile_w == 16 && vs.tile_h == 16)
+        bwd_launch<16, 16, BM>(vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, cp, queue, s);
+    else if (vs.tile_w == 8 && vs.tile_h == 8)
+        bwd_launch<8, 8, BM>(vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, cp, queue, s);
+    else if (vs.tile_w == 32 && vs.tile_h == 16)
+        bwd_launch<32, 16, BM>(vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, cp, queue, s);
 }
 
 } // namespace
 
+void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t *n_chunks, uint32_t *n_slots,
+                         cudaStream_t s) {
+    if (n_tiles == 0) return;
+    int blocks = (int)((n_tiles + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    chunk_count_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, (uint32_t)L, n_chunks, n_slots);
+}
+
+void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s) {
+    if (n_tiles == 0) return;
+    int blocks = (int)((n_tiles + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    chunk_pairs_kernel<<<blocks, 256, 0, s>>>(cp.n_chunks, cp.chunk_base, cp.part_base, n_tiles,
+                                              (uint32_t *)cp.pair_tile, cp.pair_cap, cp.slot_cap, status);
+}
+
+size_t chunk_slot_bytes(int tile_w, int tile_h) { return (size_t)kFields * tile_w * tile_h * sizeof(float); }
+
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
-                          cudaStream_t s, int bm) {
+                          const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm) {
     if (vs.total_tiles == 0) return;
-    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, s);
-    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, s);
+    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
 }
 
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
-                          GGrad *g2d, cudaStream_t s, int bm) {
+                          GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm) {
     if (vs.total_tiles == 0) return;
-    if (bm == 1) bwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, s);
-    else bwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, s);
+    if (bm == 1) bwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, cp, queue, s);
+    else bwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, g, final_T, n_contrib, g2d, cp, queue, s);
 }
 
 } // namespace lvigs

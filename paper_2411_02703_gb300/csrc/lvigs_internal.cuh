@@ -116,7 +116,8 @@ void launch_compact(const uint32_t *tiles, const uint32_t *zbits, const uint32_t
                     uint32_t *keys, uint32_t *vals, int64_t n, cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs over bits [0, bits).  Stable.
-// n read from the device.  Returns 1 when the result ends in the alt buffers.
+// n read from the device (n_dev), or n_max when n_dev is null.  Returns 1 when
+// the result ends in the alt buffers.
 size_t radix_tmp_words(int64_t n_max);
 int launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                        const uint32_t *n_dev, int64_t n_max, int bits, uint32_t *tmp,
@@ -133,14 +134,34 @@ void launch_clamp_count(const uint32_t *m_dev, int64_t m_cap, uint32_t *out, cud
 void launch_debug_keys(const uint32_t *tile_ids, const uint32_t *inst_vals, const uint32_t *zbits,
                        int n_gauss, uint64_t *keys, uint32_t *vals, int64_t m, cudaStream_t s);
 
-// Compositing: one warp per 8x8 pixel block (tile_w * tile_h / 2 threads per
-// CTA); each warp stages 32 * bm Gaussians per round (bm = 1 or 2).
+// List-parallel compositing plan (device arrays, built after the tile ranges):
+// each tile's list is cut into chunks of L entries; (tile, chunk) pairs are
+// numbered tile by tile; tiles with more than one chunk own `n_chunks` slots
+// of per-pixel partial state.
+struct ChunkPlan {
+    int L;
+    const uint32_t *n_chunks;   // [tiles]
+    const uint32_t *chunk_base; // [tiles] first pair of the tile
+    const uint32_t *part_base;  // [tiles] first slot of a multi-chunk tile
+    const uint32_t *pair_tile;  // [pair_cap] tile of each pair
+    const uint32_t *n_pairs;    // device count of pairs
+    float *part;                // [slot_cap] slots of 6 x tile_w x tile_h floats
+    uint32_t pair_cap, slot_cap;
+};
+void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t *n_chunks, uint32_t *n_slots,
+                         cudaStream_t s);
+void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s);
+size_t chunk_slot_bytes(int tile_w, int tile_h);
+
+// Compositing: persistent warps, one (tile, chunk, 8x8 block) per work item;
+// each stages 32 * bm Gaussians per round (bm = 1 or 2).  `queue` is one device
+// word (the work counter; reset by the launcher).
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
-                          const GRec *recs, const ViewImages &out, float *final_T,
-                          int32_t *n_contrib, cudaStream_t s, int bm);
+                          const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
+                          const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
-                          const GRec *recs, const ViewGrads &g, const float *final_T,
-                          const int32_t *n_contrib, GGrad *g2d, cudaStream_t s, int bm);
+                          const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
+                          GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);
 
 // Loss (Eq. 10-12) over one or more views (packed per view through the arrays).
 struct LossViews {

@@ -144,12 +144,12 @@ __device__ __forceinline__ void rs_chunk(uint32_t n, int G, int b, uint32_t &beg
 }
 
 __global__ void __launch_bounds__(kRsThreads)
-radix_upsweep_kernel(const uint32_t *keys, const uint32_t *n_dev, int shift, int G,
+radix_upsweep_kernel(const uint32_t *keys, const uint32_t *n_dev, uint32_t n_host, int shift, int G,
                      uint32_t *counts) {
     __shared__ uint32_t hist[kRsWarps][256];
     for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t n = *n_dev;
+    const uint32_t n = n_dev ? *n_dev : n_host;
     uint32_t begin, end;
     rs_chunk(n, G, blockIdx.x, begin, end);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -202,7 +202,7 @@ radix_rowscan_kernel(uint32_t *counts, int G, uint32_t *totals) {
 __global__ void __launch_bounds__(kRsThreads)
 radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                        uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                       const uint32_t *n_dev, int shift, int G, const uint32_t *counts,
+                       const uint32_t *n_dev, uint32_t n_host, int shift, int G, const uint32_t *counts,
                        const uint32_t *totals) {
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_hist[kRsWarps][256];
@@ -213,7 +213,7 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
         const uint32_t dp = block_exclusive_scan_256(totals[t], &tot);
         s_base[t] = dp + counts[(size_t)t * G + blockIdx.x];
     }
-    const uint32_t n = *n_dev;
+    const uint32_t n = n_dev ? *n_dev : n_host;
     uint32_t begin, end;
     rs_chunk(n, G, blockIdx.x, begin, end);
     const uint32_t lt = lanemask_lt();
@@ -381,9 +381,10 @@ int launch_radix_sort(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
-        radix_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, n_dev, shift, G, counts);
+        radix_upsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, n_dev, (uint32_t)n_max, shift, G, counts);
         radix_rowscan_kernel<<<256, 1024, 0, s>>>(counts, G, totals);
-        radix_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, G, counts, totals);
+        radix_downsweep_kernel<<<G, kRsThreads, 0, s>>>(ki, vi, ko, vo, n_dev, (uint32_t)n_max, shift, G, counts,
+                                                        totals);
         std::swap(ki, ko);
         std::swap(vi, vo);
     }

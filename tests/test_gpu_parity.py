@@ -311,6 +311,25 @@ def test_backward_lidar_sh3(pkg):
     _backward_case(pkg, params, spec, 1)
 
 
+def test_dense_coarse_level_multi_chunk(pkg):
+    """Level 2 of a 200k-Gaussian LiDAR map: tile lists of several thousand
+    entries, composited list-parallel in chunks (forward and backward)."""
+    params, phase = lidar(200_000)
+    spec = S.trajectory_cameras(8, phase=phase)[0]  # the first keyframe of the 8-view workload
+    lv = ctx_for(pkg)
+    rgb, depth, alpha, slot = lv.render(dev_params(params), spec, 2)
+    lv.release(slot)
+    ref = O.render_view(params, ocam(spec), 2)
+    lens = ref["ranges"][:, 1].astype(np.int64) - ref["ranges"][:, 0]
+    assert lens.max() > 4 * 1024
+    exc = ref["margin"] <= MARGIN
+    e = compare_images((rgb, depth, alpha), ref, exc)
+    print(f"  longest list {lens.max()}, excused {exc.mean():.4%}, max err rgb {e[0]:.2e} alpha {e[2]:.2e}")
+    assert e[0] < IMG_TOL and e[2] < IMG_TOL
+    assert e[1] < IMG_TOL * max(1.0, float(np.abs(ref["depth"]).max()))
+    _backward_case(pkg, params, spec, 2)
+
+
 def test_autograd_function(pkg):
     params, spec, _, _ = S.small_scene(n=300, sh_degree=1)
     lv = ctx_for(pkg)
