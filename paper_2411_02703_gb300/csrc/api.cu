@@ -31,7 +31,10 @@ struct RenderState {
     DevBuf inst_a_t, inst_a_v, inst_b_t, inst_b_v;
     DevBuf ranges, final_T, n_contrib, vs_dev, counters;
     DevBuf n_chunks, chunk_base, n_slots, part_base, pair_tile, part; // list-parallel plan
+    DevBuf pair_k, pair_v, pair_k2, pair_v2, stop_at;                 // chunk-major order
+    DevBuf pix_state;                                                 // forward combine scratch
     uint32_t pair_cap = 0, slot_cap = 0;
+    int order_in_alt = 0;
     ViewSet vs{};
     GaussParams P{};
     int64_t m = 0;      // instances of the last eager build
@@ -52,6 +55,8 @@ struct RenderState {
         cp.part = (float *)part.p;
         cp.pair_cap = pair_cap;
         cp.slot_cap = slot_cap;
+        cp.pair_order = (const uint32_t *)(order_in_alt ? pair_v2.p : pair_v.p);
+        cp.stop_at = (uint32_t *)stop_at.p;
         return cp;
     }
     const uint32_t *sorted_vals() const { return (const uint32_t *)(sorted_in_b ? inst_b_v.p : inst_a_v.p); }
@@ -168,7 +173,8 @@ void release(lvigs_ctx *ctx, DevBuf &b) {
 void release_state(lvigs_ctx *ctx, RenderState &s) {
     DevBuf *all[] = {&s.recs, &s.tiles, &s.zbits, &s.rects, &s.inst_a_t, &s.inst_a_v, &s.inst_b_t,
                      &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters,
-                     &s.n_chunks, &s.chunk_base, &s.n_slots, &s.part_base, &s.pair_tile, &s.part};
+                     &s.n_chunks, &s.chunk_base, &s.n_slots, &s.part_base, &s.pair_tile, &s.part,
+                     &s.pair_k, &s.pair_v, &s.pair_k2, &s.pair_v2, &s.stop_at, &s.pix_state};
     for (DevBuf *b : all) release(ctx, *b);
     s.valid = false;
     s.m_cap = 0;
@@ -289,6 +295,12 @@ lvigs_status ensure_plan(lvigs_ctx *ctx, RenderState &st) {
     const uint64_t slots = 2 * ((uint64_t)st.m_cap / kChunkLen) + 1;
     if (pairs > 0xffffffffull || slots > 0xffffffffull) return fail(ctx, LVIGS_ERR_CAPACITY, "plan too large");
     LV_TRY(ensure(ctx, st.pair_tile, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.pair_k, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.pair_v, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.pair_k2, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.pair_v2, (size_t)pairs * 4));
+    LV_TRY(ensure(ctx, st.stop_at, (size_t)st.vs.total_pixels * 4));
+    LV_TRY(ensure(ctx, st.pix_state, (size_t)st.vs.total_pixels * pix_state_bytes()));
     LV_TRY(ensure(ctx, st.part, (size_t)slots * chunk_slot_bytes(st.vs.tile_w, st.vs.tile_h)));
     st.pair_cap = (uint32_t)pairs;
     st.slot_cap = (uint32_t)slots;
@@ -393,6 +405,12 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
         launch_scan((const uint32_t *)st.n_slots.p, nullptr, 0, (uint32_t *)st.part_base.p, cnt + 5, nullptr,
                     st.vs.total_tiles, (uint32_t *)ctx->scan_tmp.p, s);
         launch_chunk_pairs(st.plan(), st.vs.total_tiles, (uint32_t *)ctx->status.p, s);
+        // chunk-major work order (stable by pair) and the per-pixel stop record
+        launch_pair_keys(st.plan(), st.vs.total_tiles, (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
+        st.order_in_alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p,
+                                            (uint32_t *)st.pair_k2.p, (uint32_t *)st.pair_v2.p, cnt + 4,
+                                            st.pair_cap, 16, (uint32_t *)ctx->radix_tmp.p, s);
+        LV_CUDA(cudaMemsetAsync(st.stop_at.p, 0xff, (size_t)st.vs.total_pixels * 4, s));
     }
     return LVIGS_OK;
 }
@@ -558,7 +576,7 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
                              (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(),
-                             (uint32_t *)st.counters.p + 3, s, ctx->bm);
+                             (uint32_t *)st.counters.p + 3, st.pix_state.p, s, ctx->bm);
     }
     LV_CUDA(cudaGetLastError());
     st.valid = true;
@@ -838,7 +856,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
                              (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
-                             s, ctx->bm);
+                             st.pix_state.p, s, ctx->bm);
     }
     // 4. a8: loss and its image gradients for every view
     {

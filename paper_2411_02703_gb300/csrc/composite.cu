@@ -15,14 +15,17 @@
 //            final here.  For a longer list the walk starts from T = 1 and
 //            stores the chunk's local sums (colour, depth, T, last contributor,
 //            whether the local T hit the stop, which implies the global stop
-//            lies at or before that Gaussian).
+//            lies at or before that Gaussian).  Items run chunk-major (all
+//            first chunks, then all second chunks, ...) and a pixel whose local
+//            stop is published for an earlier chunk (a per-pixel atomicMin) is
+//            skipped by later chunks: they cannot contribute to it.
 //   phase 2  per pixel the chunks are combined in order: C += T C_k,
-//            T *= T_k, until the chunk whose end would cross 1e-4; that one
-//            chunk is walked again from the true T to find the exact stop.
-//            The pass then stores, for each chunk, the transmittance at its end
-//            and the normalised sums of everything composited after it (all
-//            terms non-negative, so no cancellation), which is the state the
-//            backward walk of that chunk starts from.
+//            T *= T_k, until the chunk whose end would cross 1e-4 (2a); that
+//            chunk is walked again from the true T to find the exact stop, one
+//            (tile, chunk, block) item per warp (2b); then every chunk gets the
+//            transmittance at its end and the normalised sums of everything
+//            composited after it (all terms non-negative, so no cancellation),
+//            the state the backward walk of that chunk starts from (2c).
 // Within a walk the list is consumed in batches of 32*BM: each lane gathers
 // records and tests them against the block with the conservative box of the
 // region where alpha can reach 1/255 (half-extents from preprocessing); the
@@ -211,8 +214,9 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     for (;;) {
         const uint32_t item = take_item(queue, lane);
         if (item >= n_items) break;
-        const uint32_t pair = item / Gm::NB;
+        const uint32_t pair = cp.pair_order ? cp.pair_order[item / Gm::NB] : item / Gm::NB;
         const int blk = (int)(item % Gm::NB);
+        if (pair >= cp.pair_cap) continue;
         const uint32_t gt = cp.pair_tile[pair];
         if (gt >= vsp->total_tiles) continue; // never written (capacity overflow, latched)
         const uint32_t nch = cp.n_chunks[gt];
@@ -234,9 +238,19 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
             last[j] = 0;
             done[j] = !(bp.px < V.W && bp.py0 + j < V.H);
             stopped[j] = false;
+            // a pixel known to stop in an earlier chunk needs nothing from this one
+            if (!done[j] && nch > 1) {
+                const size_t gp = V.pix_base + (size_t)(bp.py0 + j) * V.W + bp.px;
+                if (__ldcg(cp.stop_at + gp) < k) done[j] = true;
+            }
         }
         fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2,
                      D, last, done, stopped);
+        if (nch > 1) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+                if (stopped[j]) atomicMin(cp.stop_at + V.pix_base + (size_t)(bp.py0 + j) * V.W + bp.px, k);
+        }
         if (nch <= 1) {
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
@@ -260,18 +274,24 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     }
 }
 
-// Phase 2: combine the chunks of multi-chunk tiles, one (tile, block) per warp.
-template <int TW, int TH, int BM>
+// Per-pixel state between the combine kernels (multi-chunk tiles only):
+// stop chunk (or -1), transmittance before it, colour / depth before it, last.
+struct PixState {
+    int stop;
+    float Tin, C0, C1, C2, D;
+    int last;
+    int pad;
+};
+
+// Phase 2a: per pixel, combine chunks in order up to the one whose end would
+// cross the 1e-4 stop (or whose walk stopped locally).  Pixels that never stop
+// are final here.
+template <int TW, int TH>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-composite_combine_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
-                         const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
-                         float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
-                         uint32_t total_tiles) {
+combine_scan_kernel(const ViewSet *__restrict__ vsp, ViewImages out, float *__restrict__ final_T,
+                    int32_t *__restrict__ n_contrib, ChunkPlan cp, PixState *__restrict__ ps, uint32_t total_tiles) {
     using Gm = Geometry<TW, TH>;
-    constexpr int B = 32 * BM;
     constexpr int TPX = Gm::TPX;
-    __shared__ float4 sA[kWarpsPerCta][B], sB[kWarpsPerCta][B], sC[kWarpsPerCta][B];
-    __shared__ int sP[kWarpsPerCta][B];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t item = blockIdx.x * kWarpsPerCta + w;
     if (item >= total_tiles * Gm::NB) return;
@@ -281,110 +301,163 @@ composite_combine_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restric
     if (nch <= 1) return;
     const uint32_t s0 = cp.part_base[gt];
     if (s0 + nch > cp.slot_cap) return; // capacity overflow is latched by the planner
-    const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
     const int vi = view_of_tile(*vsp, gt);
     const ViewDesc &V = vsp->v[vi];
     const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
-    const uint2 rg = ranges[gt];
-
-    // pass 1: running combination up to the chunk where the pixel stops
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT];
-    int last[PPT], stop[PPT];
-    bool inside[PPT];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-        T[j] = 1.f;
-        C0[j] = C1[j] = C2[j] = D[j] = 0.f;
-        last[j] = 0;
-        stop[j] = -1;
-        Tin[j] = 1.f;
-        inside[j] = bp.px < V.W && bp.py0 + j < V.H;
-    }
-    for (uint32_t k = 0; k < nch; ++k) {
-#pragma unroll
-        for (int j = 0; j < PPT; ++j) {
-            if (!inside[j] || stop[j] >= 0) continue;
-            const int lp = bp.lp0 + j * TW;
+        const int py = bp.py0 + j;
+        if (!(bp.px < V.W && py < V.H)) continue;
+        const int lp = bp.lp0 + j * TW;
+        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+        int last = 0, stop = -1;
+        for (uint32_t k = 0; k < nch; ++k) {
             const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
             const int lk = __float_as_int(slot_field(cp, s0 + k, 5, TPX)[lp]);
-            const float Tn = __fmul_rn(T[j], Tk);
+            const float Tn = __fmul_rn(T, Tk);
             if ((lk & (int)0x80000000) || Tn < kTMin) {
-                stop[j] = (int)k;
-                Tin[j] = T[j];
-                continue;
+                stop = (int)k;
+                break;
             }
-            C0[j] = fmaf(T[j], slot_field(cp, s0 + k, 0, TPX)[lp], C0[j]);
-            C1[j] = fmaf(T[j], slot_field(cp, s0 + k, 1, TPX)[lp], C1[j]);
-            C2[j] = fmaf(T[j], slot_field(cp, s0 + k, 2, TPX)[lp], C2[j]);
-            D[j] = fmaf(T[j], slot_field(cp, s0 + k, 3, TPX)[lp], D[j]);
-            T[j] = Tn;
-            if (lk) last[j] = lk;
+            C0 = fmaf(T, slot_field(cp, s0 + k, 0, TPX)[lp], C0);
+            C1 = fmaf(T, slot_field(cp, s0 + k, 1, TPX)[lp], C1);
+            C2 = fmaf(T, slot_field(cp, s0 + k, 2, TPX)[lp], C2);
+            D = fmaf(T, slot_field(cp, s0 + k, 3, TPX)[lp], D);
+            T = Tn;
+            if (lk) last = lk;
         }
+        const size_t gp = V.pix_base + (size_t)py * V.W + bp.px;
+        ps[gp] = PixState{stop, T, C0, C1, C2, D, last, 0};
+        if (stop < 0) write_final(V, out, vi, final_T, n_contrib, bp.px, py, T, C0, C1, C2, D, last);
     }
-    // pass 2: exact walk of the stop chunk from the true transmittance
-    float rC0[PPT], rC1[PPT], rC2[PPT], rD[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-        rC0[j] = C0[j];
-        rC1[j] = C1[j];
-        rC2[j] = C2[j];
-        rD[j] = D[j];
-    }
-    for (uint32_t k = 0; k < nch; ++k) {
-        const bool need = (stop[0] == (int)k) || (stop[1] == (int)k);
-        if (!__any_sync(0xffffffffu, need)) continue;
+}
+
+// Phase 2b: exact walk of each stop chunk from the true transmittance, one
+// (tile, chunk, block) item per warp, for the pixels that stop in that chunk.
+// Writes their final values and the chunk's contribution (backward state).
+template <int TW, int TH, int BM>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+combine_walk_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
+                    const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
+                    float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
+                    const PixState *__restrict__ ps, uint32_t *__restrict__ queue) {
+    using Gm = Geometry<TW, TH>;
+    constexpr int B = 32 * BM;
+    constexpr int TPX = Gm::TPX;
+    __shared__ float4 sA[kWarpsPerCta][B], sB[kWarpsPerCta][B], sC[kWarpsPerCta][B];
+    __shared__ int sP[kWarpsPerCta][B];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
+    const uint32_t n_items = min(*cp.n_pairs, cp.pair_cap) * Gm::NB;
+    for (;;) {
+        const uint32_t item = take_item(queue, lane);
+        if (item >= n_items) break;
+        const uint32_t pair = cp.pair_order ? cp.pair_order[item / Gm::NB] : item / Gm::NB;
+        const int blk = (int)(item % Gm::NB);
+        if (pair >= cp.pair_cap) continue;
+        const uint32_t gt = cp.pair_tile[pair];
+        if (gt >= vsp->total_tiles) continue;
+        const uint32_t nch = cp.n_chunks[gt];
+        const uint32_t k = pair - cp.chunk_base[gt];
+        if (nch <= 1 || k >= nch || cp.part_base[gt] + nch > cp.slot_cap) continue;
+        const int vi = view_of_tile(*vsp, gt);
+        const ViewDesc &V = vsp->v[vi];
+        const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT], b0[PPT], b1[PPT], b2[PPT], bd[PPT];
+        int last[PPT];
         bool done[PPT], stopped[PPT];
+        bool any = false;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
-            done[j] = stop[j] != (int)k;
+            done[j] = true;
             stopped[j] = false;
+            T[j] = Tin[j] = 1.f;
+            C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+            last[j] = 0;
+            const int py = bp.py0 + j;
+            if (bp.px < V.W && py < V.H) {
+                const PixState st = ps[V.pix_base + (size_t)py * V.W + bp.px];
+                if (st.stop == (int)k) {
+                    done[j] = false;
+                    any = true;
+                    T[j] = Tin[j] = st.Tin;
+                    C0[j] = st.C0;
+                    C1[j] = st.C1;
+                    C2[j] = st.C2;
+                    D[j] = st.D;
+                    last[j] = st.last;
+                }
+            }
+            b0[j] = C0[j];
+            b1[j] = C1[j];
+            b2[j] = C2[j];
+            bd[j] = D[j];
         }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        const uint2 rg = ranges[gt];
         const uint32_t lo = rg.x + k * (uint32_t)cp.L;
         const uint32_t hi = min(rg.y, lo + (uint32_t)cp.L);
         fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2, D,
                      last, done, stopped);
-    }
+        const uint32_t slot = cp.part_base[gt] + k;
 #pragma unroll
-    for (int j = 0; j < PPT; ++j)
-        write_final(V, out, vi, final_T, n_contrib, bp.px, bp.py0 + j, T[j], C0[j], C1[j], C2[j], D[j], last[j]);
+        for (int j = 0; j < PPT; ++j) {
+            const int py = bp.py0 + j;
+            if (!(bp.px < V.W && py < V.H)) continue;
+            if (ps[V.pix_base + (size_t)py * V.W + bp.px].stop != (int)k) continue;
+            write_final(V, out, vi, final_T, n_contrib, bp.px, py, T[j], C0[j], C1[j], C2[j], D[j], last[j]);
+            const int lp = bp.lp0 + j * TW;
+            slot_field(cp, slot, 0, TPX)[lp] = C0[j] - b0[j];
+            slot_field(cp, slot, 1, TPX)[lp] = C1[j] - b1[j];
+            slot_field(cp, slot, 2, TPX)[lp] = C2[j] - b2[j];
+            slot_field(cp, slot, 3, TPX)[lp] = D[j] - bd[j];
+            slot_field(cp, slot, 4, TPX)[lp] = Tin[j] - T[j];
+            slot_field(cp, slot, 5, TPX)[lp] = T[j];
+        }
+    }
+}
 
-    // pass 3: per chunk, the transmittance at its end and the normalised sums
-    // of everything composited after it (the backward walk's starting state).
+// Phase 2c: per chunk, the transmittance at its end and the normalised sums of
+// everything composited after it: the state the backward walk of the chunk
+// starts from.  All summed terms are non-negative (no cancellation).
+template <int TW, int TH>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+combine_state_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp, const PixState *__restrict__ ps,
+                     uint32_t total_tiles) {
+    using Gm = Geometry<TW, TH>;
+    constexpr int TPX = Gm::TPX;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t item = blockIdx.x * kWarpsPerCta + w;
+    if (item >= total_tiles * Gm::NB) return;
+    const uint32_t gt = item / Gm::NB;
+    const int blk = (int)(item % Gm::NB);
+    const uint32_t nch = cp.n_chunks[gt];
+    if (nch <= 1) return;
+    const uint32_t s0 = cp.part_base[gt];
+    if (s0 + nch > cp.slot_cap) return;
+    const int vi = view_of_tile(*vsp, gt);
+    const ViewDesc &V = vsp->v[vi];
+    const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
-        if (!inside[j]) continue;
+        const int py = bp.py0 + j;
+        if (!(bp.px < V.W && py < V.H)) continue;
         const int lp = bp.lp0 + j * TW;
-        // 3a: each slot becomes (contribution of the chunk to C, D, V; T at its end)
+        const int stop = ps[V.pix_base + (size_t)py * V.W + bp.px].stop;
+        const uint32_t top = stop >= 0 ? (uint32_t)stop : nch - 1;
+        // each slot before the stop chunk becomes (its contribution, T at its end);
+        // the stop chunk's slot was written by the exact walk
         float t = 1.f;
-        const uint32_t top = stop[j] >= 0 ? (uint32_t)stop[j] : nch - 1;
-        for (uint32_t k = 0; k <= top; ++k) {
-            float g0, g1, g2, gd, ga, tend;
-            if ((int)k == stop[j]) {
-                g0 = C0[j] - rC0[j];
-                g1 = C1[j] - rC1[j];
-                g2 = C2[j] - rC2[j];
-                gd = D[j] - rD[j];
-                ga = Tin[j] - T[j];
-                tend = T[j];
-            } else {
-                const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
-                g0 = t * slot_field(cp, s0 + k, 0, TPX)[lp];
-                g1 = t * slot_field(cp, s0 + k, 1, TPX)[lp];
-                g2 = t * slot_field(cp, s0 + k, 2, TPX)[lp];
-                gd = t * slot_field(cp, s0 + k, 3, TPX)[lp];
-                tend = __fmul_rn(t, Tk);
-                ga = t - tend;
-            }
-            slot_field(cp, s0 + k, 0, TPX)[lp] = g0;
-            slot_field(cp, s0 + k, 1, TPX)[lp] = g1;
-            slot_field(cp, s0 + k, 2, TPX)[lp] = g2;
-            slot_field(cp, s0 + k, 3, TPX)[lp] = gd;
-            slot_field(cp, s0 + k, 4, TPX)[lp] = ga;
+        for (uint32_t k = 0; k < top || (stop < 0 && k == top); ++k) {
+            const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
+            const float tend = __fmul_rn(t, Tk);
+#pragma unroll
+            for (int f = 0; f < 4; ++f) slot_field(cp, s0 + k, f, TPX)[lp] *= t;
+            slot_field(cp, s0 + k, 4, TPX)[lp] = t - tend;
             slot_field(cp, s0 + k, 5, TPX)[lp] = tend;
             t = tend;
         }
-        // 3b: suffix sums, normalised by the transmittance at each chunk's end
-        float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         for (int k = (int)top; k >= 0; --k) {
             float g[5];
 #pragma unroll
@@ -393,8 +466,8 @@ composite_combine_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restric
             const float inv = tend > 0.f ? 1.f / tend : 0.f;
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
-                slot_field(cp, s0 + k, f, TPX)[lp] = s[f] * inv;
-                s[f] += g[f];
+                slot_field(cp, s0 + k, f, TPX)[lp] = acc[f] * inv;
+                acc[f] += g[f];
             }
         }
     }
@@ -460,8 +533,9 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     for (;;) {
         const uint32_t item = take_item(queue, lane);
         if (item >= n_items) break;
-        const uint32_t pair = item / Gm::NB;
+        const uint32_t pair = cp.pair_order ? cp.pair_order[item / Gm::NB] : item / Gm::NB;
         const int blk = (int)(item % Gm::NB);
+        if (pair >= cp.pair_cap) continue;
         const uint32_t gt = cp.pair_tile[pair];
         if (gt >= vsp->total_tiles) continue; // never written (capacity overflow, latched)
         const uint32_t nch = cp.n_chunks[gt];
@@ -598,6 +672,19 @@ __global__ void chunk_pairs_kernel(const uint32_t *__restrict__ n_chunks, const 
     }
 }
 
+// Sort keys for chunk-major work order: the chunk index of every pair.
+__global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const uint32_t *__restrict__ chunk_base,
+                                 const uint32_t *n_pairs, uint32_t pair_cap, uint32_t n_tiles,
+                                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const uint32_t n = min(*n_pairs, pair_cap);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const uint32_t t = pair_tile[p];
+        const uint32_t k = t < n_tiles ? p - chunk_base[t] : 0xffffu;
+        keys[p] = k < 0xffffu ? k : 0xffffu;
+        vals[p] = p;
+    }
+}
+
 template <typename K>
 unsigned persistent_grid(K kernel, uint64_t max_items) {
     int dev = 0, sms = 152, per_sm = 1;
@@ -613,17 +700,22 @@ unsigned persistent_grid(K kernel, uint64_t max_items) {
 template <int TW, int TH, int BM>
 void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                 const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
-                uint32_t *queue, cudaStream_t s) {
+                uint32_t *queue, void *pix_state, cudaStream_t s) {
     using Gm = Geometry<TW, TH>;
-    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    PixState *ps = (PixState *)pix_state;
     const uint64_t max_items = (uint64_t)cp.pair_cap * Gm::NB;
+    const uint64_t tw = (uint64_t)vs.total_tiles * Gm::NB;
+    const unsigned grid_tiles = (unsigned)((tw + kWarpsPerCta - 1) / kWarpsPerCta);
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
     composite_fwd_kernel<TW, TH, BM><<<persistent_grid(composite_fwd_kernel<TW, TH, BM>, max_items),
                                        kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
                                                                   n_contrib, cp, queue);
-    const uint64_t tw = (uint64_t)vs.total_tiles * Gm::NB;
-    composite_combine_kernel<TW, TH, BM><<<(unsigned)((tw + kWarpsPerCta - 1) / kWarpsPerCta), kWarpsPerCta * 32,
-                                           0, s>>>(vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp,
-                                                   vs.total_tiles);
+    combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, out, final_T, n_contrib, cp, ps,
+                                                                        vs.total_tiles);
+    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    combine_walk_kernel<TW, TH, BM><<<persistent_grid(combine_walk_kernel<TW, TH, BM>, max_items), kWarpsPerCta * 32,
+                                      0, s>>>(vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, ps, queue);
+    combine_state_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, cp, ps, vs.total_tiles);
 }
 
 template <int TW, int TH, int BM>
@@ -641,13 +733,13 @@ void bwd_launch(const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_va
 template <int BM>
 void fwd_dispatch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                   const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
-                  uint32_t *queue, cudaStream_t s) {
+                  uint32_t *queue, void *pix_state, cudaStream_t s) {
     if (vs.tile_w == 16 && vs.tile_h == 16)
-        fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+        fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
     else if (vs.tile_w == 8 && vs.tile_h == 8)
-        fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+        fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
     else if (vs.tile_w == 32 && vs.tile_h == 16)
-        fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+        fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
 }
 
 template <int BM>
@@ -680,14 +772,23 @@ void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status,
                                               (uint32_t *)cp.pair_tile, cp.pair_cap, cp.slot_cap, status);
 }
 
+void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+    if (cp.pair_cap == 0) return;
+    int blocks = (int)((cp.pair_cap + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    pair_keys_kernel<<<blocks, 256, 0, s>>>(cp.pair_tile, cp.chunk_base, cp.n_pairs, cp.pair_cap, n_tiles, keys, vals);
+}
+
 size_t chunk_slot_bytes(int tile_w, int tile_h) { return (size_t)kFields * tile_w * tile_h * sizeof(float); }
+
+size_t pix_state_bytes() { return sizeof(PixState); }
 
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
-                          const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm) {
+                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm) {
     if (vs.total_tiles == 0) return;
-    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
-    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, s);
+    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
+    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
 }
 
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,

@@ -147,18 +147,23 @@ struct ChunkPlan {
     const uint32_t *n_pairs;    // device count of pairs
     float *part;                // [slot_cap] slots of 6 x tile_w x tile_h floats
     uint32_t pair_cap, slot_cap;
+    const uint32_t *pair_order; // [pair_cap] work order (chunk-major), or null
+    uint32_t *stop_at;          // [total pixels] first chunk with a local stop (reset to ~0)
 };
 void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t *n_chunks, uint32_t *n_slots,
                          cudaStream_t s);
 void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s);
+void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s);
 size_t chunk_slot_bytes(int tile_w, int tile_h);
 
 // Compositing: persistent warps, one (tile, chunk, 8x8 block) per work item;
 // each stages 32 * bm Gaussians per round (bm = 1 or 2).  `queue` is one device
 // word (the work counter; reset by the launcher).
+// pix_state: pix_state_bytes() per pixel of the view set (forward scratch).
+size_t pix_state_bytes();
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
-                          const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);
+                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm);
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
                           GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);
