@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="auto", help="WxH, or auto (autotuned)")
     ap.add_argument("--batch-depth", type=int, default=0)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
@@ -152,7 +152,7 @@ def run_ours(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    tile = tuple(int(x) for x in args.tile.split("x"))
+    tile = (16, 16) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
     wl = S.workload(args.workload)
     params = wl["params"]
     cams, levels = wl["cams"], wl["levels"]
@@ -183,6 +183,12 @@ def run_ours(args):
 
     def step():
         lv.train_step_batched(dev, cams, levels, gts, lis, lam, lamd, grads=grads)
+
+    autotune = None
+    if args.tile == "auto":
+        t_best, bd_best, times = lv.autotune(dev, cams, levels, gts, lis, lam, lamd, trials=3, grads=grads)
+        autotune = {"chosen": f"{t_best[0]}x{t_best[1]}/{bd_best}", "ms_per_step": times}
+        tile = t_best
 
     # warm-up (first call sizes the workspace eagerly, the second captures the graph)
     for _ in range(max(3, args.warmup)):
@@ -304,8 +310,8 @@ def run_ours(args):
         "dtype": "f32",
         "data": "synthetic (seeded LiDAR-sweep scene and procedural targets)",
         "config": {"workload": args.workload, "gaussians": N, "views": V, "levels": levels,
-                   "base_resolution": "1280x1024", "sh_degree": int(params["sh_degree"]), "tile": args.tile,
-                   "batch_depth": args.batch_depth or "auto",
+                   "base_resolution": "1280x1024", "sh_degree": int(params["sh_degree"]),
+                   "tile": f"{tile[0]}x{tile[1]}", "autotune": autotune,
                    "loss": "0.8 L1 + 0.2 (1-SSIM) + 0.1 depth L1", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (236 MB of parameters per step)"},
         "mpix_per_s": round(world * pix * steps_per_s / 1e6, 3),

@@ -181,6 +181,17 @@ lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gaussians *g,
                                       const lvigs_batch *batch, const lvigs_grads *grads,
                                       void *stream);
 
+/* Autotuner of the batched step (a10): times `trials` graph replays of the
+ * step for each candidate (tile 16x16, 8x8, 32x16) x (batch depth 64, 32) and
+ * leaves the context configured with the fastest, which is written to
+ * *chosen (ms_out, optional, receives the 6 per-step times in that order).
+ * The tile size is part of what is computed (a pixel composites the Gaussians
+ * whose rectangle covers its tile), so results follow the chosen tile size.
+ * The candidate steps write `grads` and `batch->losses` like a normal step. */
+lvigs_status lvigs_autotune_batched(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *batch,
+                                    const lvigs_grads *grads, int trials, void *stream,
+                                    lvigs_config *chosen, double *ms_out);
+
 /* Parity hooks: the sorted 64-bit keys ((tile id << 32) | float bits of depth)
  * and Gaussian indices of `view_slot`.  With keys == NULL only *m is set.
  * keys/vals are device pointers with room for *m entries on input (m_cap). */

@@ -83,10 +83,14 @@ SIGNATURES = {
     "lvigs_release_view": (_I, [_P, _I]),
     "lvigs_last_error": (ctypes.c_char_p, [_P]),
     "lvigs_step_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), _P]),
+    "lvigs_autotune_batched": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Batch), ctypes.POINTER(Grads), _I,
+                                    _P, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double)]),
     "lvigs_profile_enable": (_I, [_P, _I]),
     "lvigs_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(_I)]),
 }
+
+AUTOTUNE_CANDIDATES = [((16, 16), 64), ((16, 16), 32), ((8, 8), 64), ((8, 8), 32), ((32, 16), 64), ((32, 16), 32)]
 
 PHASES = ["preprocess", "compact", "depth_sort", "offsets", "emit", "tile_sort", "ranges", "composite_fwd",
           "loss", "composite_bwd", "preprocess_bwd", "pyramid"]

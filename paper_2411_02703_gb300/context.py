@@ -145,23 +145,19 @@ class Context:
         return r2, d2
 
     # -- batched path ------------------------------------------------------
-    def train_step_batched(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, grads=None,
-                           accumulate=False, host_targets=False, host_loss=False, graph=True, outputs=None,
-                           losses=None):
-        """One batched step (a10): render, loss and backward of every view.
-
-        gts / lidars are level-0 targets (CUDA tensors, or pinned CPU tensors with
-        host_targets=True).  Returns (losses [V,4] float64, grads).
-        """
+    def _batch(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, grads, accumulate, host_targets,
+               host_loss, graph, outputs, losses):
         V = len(cams)
         g = gaussians_struct(params)
         if grads is None:
             grads = {k: torch.zeros_like(params[k]) for k in PARAM_NAMES}
         gs = L.Grads(*(grads[k].data_ptr() for k in PARAM_NAMES), int(bool(accumulate)))
+        keep = []  # ctypes arrays referenced by the Batch struct
         camarr = (L.Camera * V)(*[camera_struct(c) for c in cams])
         lvl = (ctypes.c_int * V)(*[int(x) for x in levels])
         gtp = (ctypes.c_void_p * V)(*[t.data_ptr() for t in gts])
         lip = (ctypes.c_void_p * V)(*[t.data_ptr() if t is not None else None for t in lidars])
+        keep += [camarr, lvl, gtp, lip]
         if losses is None:
             losses = torch.zeros((V, 4), dtype=torch.float64,
                                  device="cpu" if host_loss else params["means"].device)
@@ -177,12 +173,42 @@ class Context:
                    | (0 if graph else L.STEP_NO_GRAPH))
         b.losses = losses.data_ptr()
         if outputs is not None:
-            b.rgb_out = (ctypes.c_void_p * V)(*[o[0].data_ptr() for o in outputs])
-            b.depth_out = (ctypes.c_void_p * V)(*[o[1].data_ptr() for o in outputs])
-            b.alpha_out = (ctypes.c_void_p * V)(*[o[2].data_ptr() for o in outputs])
+            for i, nm in enumerate(("rgb_out", "depth_out", "alpha_out")):
+                arr = (ctypes.c_void_p * V)(*[o[i].data_ptr() for o in outputs])
+                keep.append(arr)
+                setattr(b, nm, arr)
+        return g, b, gs, grads, losses, keep
+
+    def train_step_batched(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, grads=None,
+                           accumulate=False, host_targets=False, host_loss=False, graph=True, outputs=None,
+                           losses=None):
+        """One batched step (a10): render, loss and backward of every view.
+
+        gts / lidars are level-0 targets (CUDA tensors, or pinned CPU tensors with
+        host_targets=True).  Returns (losses [V,4] float64, grads).
+        """
+        g, b, gs, grads, losses, keep = self._batch(params, cams, levels, gts, lidars, lambda_ssim, lambda_depth,
+                                                    grads, accumulate, host_targets, host_loss, graph, outputs,
+                                                    losses)
         self._chk(self._lib.lvigs_train_step_batched(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(gs),
                                                      _stream()), "lvigs_train_step_batched")
+        del keep
         return losses, grads
+
+    def autotune(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, trials=3, grads=None):
+        """Pick tile size and batch depth by timing the batched step; returns
+        ((tile_w, tile_h), batch_depth, {candidate: ms per step})."""
+        g, b, gs, grads, losses, keep = self._batch(params, cams, levels, gts, lidars, lambda_ssim, lambda_depth,
+                                                    grads, False, False, False, True, None, None)
+        cfg = L.Config()
+        ms = (ctypes.c_double * len(L.AUTOTUNE_CANDIDATES))()
+        self._chk(self._lib.lvigs_autotune_batched(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(gs),
+                                                   int(trials), _stream(), ctypes.byref(cfg), ms),
+                  "lvigs_autotune_batched")
+        del keep
+        self.tile = (cfg.tile_w, cfg.tile_h)
+        times = {f"{c[0][0]}x{c[0][1]}/{c[1]}": round(ms[i], 4) for i, c in enumerate(L.AUTOTUNE_CANDIDATES)}
+        return self.tile, cfg.batch_depth, times
 
     # -- parity hooks ------------------------------------------------------
     def debug_keys(self, slot):

@@ -900,6 +900,9 @@ BatchKey make_key(const lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_ba
     };
     add(ctx->ws_epoch);
     add((uint64_t)ctx->batch.m_cap);
+    add((uint64_t)ctx->cfg.tile_w);
+    add((uint64_t)ctx->cfg.tile_h);
+    add((uint64_t)ctx->bm);
     add((uint64_t)g->n);
     add((uint64_t)g->sh_degree);
     add((uint64_t)g->sh_stride_k);
@@ -1035,5 +1038,71 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
         std::memcpy(b->losses, ctx->host_losses, (size_t)b->n_views * 4 * sizeof(double));
     }
     LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}
+
+// ===========================================================================
+// Autotuner (a10): tile size and compositing batch depth by measurement
+// ===========================================================================
+extern "C" lvigs_status lvigs_autotune_batched(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *b,
+                                               const lvigs_grads *gr, int trials, void *stream,
+                                               lvigs_config *chosen, double *ms_out) {
+    if (!ctx || !b || !gr || trials < 1) return ctx ? fail(ctx, LVIGS_ERR_INVALID_ARG, "bad autotune arguments")
+                                                    : LVIGS_ERR_INVALID_ARG;
+    struct Cand {
+        int tw, th, bm;
+    };
+    const Cand cands[] = {{16, 16, 2}, {16, 16, 1}, {8, 8, 2}, {8, 8, 1}, {32, 16, 2}, {32, 16, 1}};
+    const int nc = (int)(sizeof(cands) / sizeof(cands[0]));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LV_CUDA(cudaEventCreate(&e0));
+    LV_CUDA(cudaEventCreate(&e1));
+    const lvigs_config saved = ctx->cfg;
+    const int saved_bm = ctx->bm;
+    double best = 1e30;
+    int best_i = -1;
+    lvigs_batch bb = *b;
+    bb.flags &= ~(LVIGS_STEP_HOST_LOSS | LVIGS_STEP_NO_GRAPH);
+    lvigs_status st = LVIGS_OK;
+    for (int i = 0; i < nc && st == LVIGS_OK; ++i) {
+        ctx->cfg.tile_w = cands[i].tw;
+        ctx->cfg.tile_h = cands[i].th;
+        ctx->bm = cands[i].bm;
+        ctx->batch.m_cap = 0; // size the instance list again for this tile size
+        ctx->step_pending = false;
+        // one eager step sizes the workspace, one more captures the graph
+        for (int w = 0; w < 2 && st == LVIGS_OK; ++w) st = lvigs_train_step_batched(ctx, g, &bb, gr, stream);
+        if (st != LVIGS_OK) break;
+        cudaEventRecord(e0, s);
+        for (int t = 0; t < trials && st == LVIGS_OK; ++t) st = lvigs_train_step_batched(ctx, g, &bb, gr, stream);
+        cudaEventRecord(e1, s);
+        if (st != LVIGS_OK) break;
+        LV_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / trials;
+        if (ms_out) ms_out[i] = per;
+        if (per < best) {
+            best = per;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LVIGS_OK || best_i < 0) {
+        ctx->cfg = saved;
+        ctx->bm = saved_bm;
+        ctx->batch.m_cap = 0;
+        return st != LVIGS_OK ? st : fail(ctx, LVIGS_ERR_STATE, "autotune measured nothing");
+    }
+    ctx->cfg.tile_w = cands[best_i].tw;
+    ctx->cfg.tile_h = cands[best_i].th;
+    ctx->bm = cands[best_i].bm;
+    ctx->cfg.batch_depth = 32 * cands[best_i].bm;
+    ctx->batch.m_cap = 0;
+    ctx->step_pending = false;
+    // view slots rendered with another tile size stay valid (they keep their own view set)
+    if (chosen) *chosen = ctx->cfg;
     return LVIGS_OK;
 }

@@ -405,3 +405,29 @@ def test_batched_matches_plain_and_oracle(pkg):
     excl = np.array(sorted(excl), dtype=np.int64)
     for k in pkg.PARAM_NAMES:
         grad_check(k, grads[k].cpu().numpy(), rgrads[k], excl, rtol=2e-3)
+
+
+def test_autotune_then_batched_matches_plain(pkg):
+    """The autotuner leaves a valid configuration; a batched step with it equals
+    plain renders at the chosen tile size."""
+    params, phase = lidar(30_000)
+    cams = S.trajectory_cameras(3, phase=phase, W=320, H=256, f=215.0)
+    levels = [0, 1, 2]
+    tg = [S.target_images(c, 200 + i) for i, c in enumerate(cams)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dp = dev_params(params)
+    gts, lis = [t(x[0]) for x in tg], [t(x[1]) for x in tg]
+    lv = pkg.Context()
+    tile, bd, times = lv.autotune(dp, cams, levels, gts, lis, 0.2, 0.1, trials=2)
+    print(f"  autotune chose {tile}/{bd}: {times}")
+    assert tile in [(16, 16), (8, 8), (32, 16)] and bd in (32, 64)
+    assert all(v > 0 for v in times.values())
+    outs = [(torch.empty(3, c.H >> l, c.W >> l, device="cuda"), torch.empty(c.H >> l, c.W >> l, device="cuda"),
+             torch.empty(c.H >> l, c.W >> l, device="cuda")) for c, l in zip(cams, levels)]
+    lv.train_step_batched(dp, cams, levels, gts, lis, 0.2, 0.1, outputs=outs)
+    torch.cuda.synchronize()
+    plain = pkg.Context(tile=tile, batch_depth=bd)
+    for i, (c, l) in enumerate(zip(cams, levels)):
+        rgb, depth, alpha, slot = plain.render(dp, c, l)
+        plain.release(slot)
+        assert torch.equal(rgb, outs[i][0]) and torch.equal(alpha, outs[i][2])
