@@ -310,7 +310,7 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
 // ---------------------------------------------------------------------------
 // Backward (a7): chain rule from the screen-space gradients of every view.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ tiles,
                       const GGrad *__restrict__ g2d, ParamGrads G) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,9 +324,14 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
     float d_mean[3] = {0.f, 0.f, 0.f};
     float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; // symmetric dL/dSigma (00,01,02,11,12,22)
     float d_op = 0.f;
-    float d_sh[16][3];
+    // SH gradient accumulators live in shared memory ([coefficient][thread],
+    // conflict-free), which keeps the thread's register count and so the
+    // occupancy of this latency-bound loop in check
+    __shared__ float s_dsh[48][128];
+    float(*d_sh)[128] = s_dsh;
+    const int tid = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) d_sh[k][0] = d_sh[k][1] = d_sh[k][2] = 0.f;
+    for (int k = 0; k < 48; ++k) s_dsh[k][tid] = 0.f;
     bool any = false;
 
     const float mx = P.means[3 * (size_t)g], my = P.means[3 * (size_t)g + 1],
@@ -478,7 +483,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
             if (k < nk) {
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    d_sh[k][ch] += Y[k] * m3[ch];
+                    d_sh[3 * k + ch][tid] += Y[k] * m3[ch];
                     w[k] += m3[ch] * __ldg(shg + 3 * k + ch);
                 }
             }
@@ -537,7 +542,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         for (int k = 0; k < 16; ++k)
             if (k < K)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = d_sh[k][ch];
+                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = d_sh[3 * k + ch][tid];
         for (int k = 16; k < K; ++k)
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = 0.f;
@@ -555,7 +560,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         for (int k = 0; k < 16; ++k)
             if (k < nk)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += d_sh[k][ch];
+                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += d_sh[3 * k + ch][tid];
     }
 }
 

@@ -27,9 +27,9 @@ constexpr int kScanTile = kScanThreads * kScanItems; // 4096
 
 constexpr int kRsWarps = 8;
 constexpr int kRsThreads = kRsWarps * 32;
-constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems; // 4096
-constexpr int kRsMaxGrid = 1024;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems; // 2048
+constexpr int kRsMaxGrid = 1024; // row scan: one thread per block of the grid
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
