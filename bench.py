@@ -125,6 +125,7 @@ def algorithmic_bytes(N, V, K, n_vis, M, P, loaded, pyr_px=0):
         "tile_sort": 2 * 20 * M,
         "ranges": M * 4,
         "composite_fwd": loaded * 52 + P * 28,
+        "combine": 0,
         "loss": P * (32 + 36 + 36 + 32 + 16),
         "composite_bwd": loaded * 52 + P * 40,
         "preprocess_bwd": 2 * prm + n_vis * 52,
@@ -132,11 +133,14 @@ def algorithmic_bytes(N, V, K, n_vis, M, P, loaded, pyr_px=0):
 
 
 def alu_flops(n_contrib_sum):
-    # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernels:
-    # forward ~20 (offset, quadratic form, alpha, transmittance, 4 accumulations),
-    # backward ~70 (the same plus dL/dalpha, five suffix sums, ten partials and
-    # a 5-level shuffle sum of 10 values amortised over 32 lanes)
-    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 70.0 * n_contrib_sum}
+    # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernel
+    # source: forward 20 (offset, quadratic form 7, exp 2, alpha 2, transmittance
+    # 2, colour/depth 5, weight 1), backward 55 (the forward's 13 to alpha, the
+    # transmittance division 2, dL/dalpha 11, five suffix sums 10, ten partials
+    # 19).  Evaluations are counted as the sum over pixels of the last
+    # contributor's list position, an upper bound (it includes list entries the
+    # 8x8-block culling skips), so the achieved rate is an upper bound too.
+    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 55.0 * n_contrib_sum}
 
 
 def run_ours(args):

@@ -223,12 +223,13 @@ enum {
     LVIGS_PHASE_EMIT = 4,           /* a2, instance emission */
     LVIGS_PHASE_TILE_SORT = 5,      /* a3, tile-id radix sort of instances */
     LVIGS_PHASE_RANGES = 6,         /* a4 */
-    LVIGS_PHASE_COMPOSITE_FWD = 7,  /* a5 */
+    LVIGS_PHASE_COMPOSITE_FWD = 7,  /* a5, per-chunk compositing */
     LVIGS_PHASE_LOSS = 8,           /* a8 */
     LVIGS_PHASE_COMPOSITE_BWD = 9,  /* a6 */
     LVIGS_PHASE_PREPROCESS_BWD = 10,/* a7 */
     LVIGS_PHASE_PYRAMID = 11,       /* a9 */
-    LVIGS_N_PHASES = 12
+    LVIGS_PHASE_COMBINE = 12,       /* a5, combine of multi-chunk tile lists */
+    LVIGS_N_PHASES = 13
 };
 lvigs_status lvigs_profile_enable(lvigs_ctx *ctx, int enable);
 /* Waits for the recorded phases; writes the summed milliseconds and call

@@ -93,7 +93,7 @@ SIGNATURES = {
 AUTOTUNE_CANDIDATES = [((16, 16), 64), ((16, 16), 32), ((8, 8), 64), ((8, 8), 32), ((32, 16), 64), ((32, 16), 32)]
 
 PHASES = ["preprocess", "compact", "depth_sort", "offsets", "emit", "tile_sort", "ranges", "composite_fwd",
-          "loss", "composite_bwd", "preprocess_bwd", "pyramid"]
+          "loss", "composite_bwd", "preprocess_bwd", "pyramid", "combine"]
 
 _lib = None
 

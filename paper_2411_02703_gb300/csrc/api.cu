@@ -572,11 +572,11 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     im.rgb[0] = out->rgb;
     im.depth[0] = out->depth;
     im.alpha[0] = out->alpha;
-    {
-        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
+    for (int part = 1; part <= 2; ++part) {
+        Phase ph(ctx, part == 1 ? LVIGS_PHASE_COMPOSITE_FWD : LVIGS_PHASE_COMBINE, s);
         launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
                              (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(),
-                             (uint32_t *)st.counters.p + 3, st.pix_state.p, s, ctx->bm);
+                             (uint32_t *)st.counters.p + 3, st.pix_state.p, s, ctx->bm, part);
     }
     LV_CUDA(cudaGetLastError());
     st.valid = true;
@@ -852,11 +852,11 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     lv.lambda_depth = b->lambda_depth;
     LV_TRY(ensure(ctx, ctx->loss_tmp, loss_tmp_bytes(lv)));
     const ViewSet *vsd = (const ViewSet *)st.vs_dev.p;
-    {
-        Phase ph(ctx, LVIGS_PHASE_COMPOSITE_FWD, s);
+    for (int part = 1; part <= 2; ++part) {
+        Phase ph(ctx, part == 1 ? LVIGS_PHASE_COMPOSITE_FWD : LVIGS_PHASE_COMBINE, s);
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
                              (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
-                             st.pix_state.p, s, ctx->bm);
+                             st.pix_state.p, s, ctx->bm, part);
     }
     // 4. a8: loss and its image gradients for every view
     {

@@ -700,22 +700,27 @@ unsigned persistent_grid(K kernel, uint64_t max_items) {
 template <int TW, int TH, int BM>
 void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                 const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
-                uint32_t *queue, void *pix_state, cudaStream_t s) {
+                uint32_t *queue, void *pix_state, int part, cudaStream_t s) {
     using Gm = Geometry<TW, TH>;
     PixState *ps = (PixState *)pix_state;
     const uint64_t max_items = (uint64_t)cp.pair_cap * Gm::NB;
     const uint64_t tw = (uint64_t)vs.total_tiles * Gm::NB;
     const unsigned grid_tiles = (unsigned)((tw + kWarpsPerCta - 1) / kWarpsPerCta);
-    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-    composite_fwd_kernel<TW, TH, BM><<<persistent_grid(composite_fwd_kernel<TW, TH, BM>, max_items),
-                                       kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
-                                                                  n_contrib, cp, queue);
-    combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, out, final_T, n_contrib, cp, ps,
-                                                                        vs.total_tiles);
-    cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-    combine_walk_kernel<TW, TH, BM><<<persistent_grid(combine_walk_kernel<TW, TH, BM>, max_items), kWarpsPerCta * 32,
-                                      0, s>>>(vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, ps, queue);
-    combine_state_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, cp, ps, vs.total_tiles);
+    if (part & 1) {
+        cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+        composite_fwd_kernel<TW, TH, BM><<<persistent_grid(composite_fwd_kernel<TW, TH, BM>, max_items),
+                                           kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
+                                                                      n_contrib, cp, queue);
+    }
+    if (part & 2) {
+        combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, out, final_T, n_contrib, cp, ps,
+                                                                            vs.total_tiles);
+        cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+        combine_walk_kernel<TW, TH, BM><<<persistent_grid(combine_walk_kernel<TW, TH, BM>, max_items),
+                                          kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
+                                                                     n_contrib, cp, ps, queue);
+        combine_state_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, cp, ps, vs.total_tiles);
+    }
 }
 
 template <int TW, int TH, int BM>
@@ -733,13 +738,13 @@ void bwd_launch(const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_va
 template <int BM>
 void fwd_dispatch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                   const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib, const ChunkPlan &cp,
-                  uint32_t *queue, void *pix_state, cudaStream_t s) {
+                  uint32_t *queue, void *pix_state, int part, cudaStream_t s) {
     if (vs.tile_w == 16 && vs.tile_h == 16)
-        fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
+        fwd_launch<16, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, part, s);
     else if (vs.tile_w == 8 && vs.tile_h == 8)
-        fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
+        fwd_launch<8, 8, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, part, s);
     else if (vs.tile_w == 32 && vs.tile_h == 16)
-        fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
+        fwd_launch<32, 16, BM>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, part, s);
 }
 
 template <int BM>
@@ -785,10 +790,10 @@ size_t pix_state_bytes() { return sizeof(PixState); }
 
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
-                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm) {
+                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm, int part) {
     if (vs.total_tiles == 0) return;
-    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
-    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, s);
+    if (bm == 1) fwd_dispatch<1>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, part, s);
+    else fwd_dispatch<2>(vs, vsd, ranges, inst_vals, recs, out, final_T, n_contrib, cp, queue, pix_state, part, s);
 }
 
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, const uint32_t *inst_vals,

@@ -163,7 +163,8 @@ size_t chunk_slot_bytes(int tile_w, int tile_h);
 size_t pix_state_bytes();
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
-                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm);
+                          const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm,
+                          int part); // part: 1 per-chunk compositing, 2 combine of long lists, 3 both
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
                           GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);

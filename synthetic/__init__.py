@@ -157,7 +157,9 @@ def lidar_scene(n, seed=BASE_SEED + 2, sh_degree=3, log_scale=(-3.0, 0.5)):
     """Gaussians initialised from a seeded LiDAR map: sweeps along the trajectory until n points.
 
     64 beams over [-25, 15] degrees, 0.2 degree azimuth, hits in [2, 60] m on a
-    ground plane plus 40 box facades; colour from a procedural texture; SH
+    ground plane plus 40 box facades, kept in acquisition order (the order a
+    map grown from keyframe point clouds stores them); colour from a
+    procedural texture; SH
     band 0 set from the colour, higher bands ~ N(0, 0.1); opacity logit
     ~ N(0,1); log-scale ~ N(log_scale); random unit quaternions.
     """
@@ -180,7 +182,9 @@ def lidar_scene(n, seed=BASE_SEED + 2, sh_degree=3, log_scale=(-3.0, 0.5)):
         if k % n_pos == 0 and total >= n:
             break
     P = np.concatenate(pts)
-    P = P[rng.choice(P.shape[0], size=n, replace=False)]
+    # subsample, keeping acquisition order (sweep by sweep, beam by beam): a map
+    # grown from keyframe point clouds stores each frame's points together
+    P = P[np.sort(rng.choice(P.shape[0], size=n, replace=False))]
     col = _texture(P)
     K = (sh_degree + 1) ** 2
     sh = np.zeros((n, K, 3), np.float32)
