@@ -35,10 +35,15 @@
 //
 // The backward pass walks each chunk in reverse from the pixel's last
 // contributor, recovering the transmittance by division (T_i = T_{i+1} /
-// (1 - alpha_i)); no per-Gaussian state is stored.  Each lane sums its two
-// pixels' ten screen-space gradient terms, the warp reduce-scatters the ten
-// sums with 12 shuffles, and the ten lanes that end with a total add it to the
-// Gaussian's gradient record with one atomic instruction.
+// (1 - alpha_i)); no per-Gaussian state is stored.  dL/dalpha needs only the
+// dot product of the upstream gradients with the sums of what lies behind a
+// Gaussian, so one running scalar per pixel replaces those five sums.  Each
+// lane sums over its two pixels ten terms: five moments of dL/dpower (times
+// dx, dy, dx^2, dx dy, dy^2; the conic enters once per Gaussian, in the
+// backward preprocess), dL/dopacity, and the colour and depth weights.  The
+// warp reduce-scatters the ten sums with 12 shuffles, and the ten lanes that
+// end with a total add it to the Gaussian's gradient record with one atomic
+// instruction.
 #include "lvigs_internal.cuh"
 
 namespace lvigs {
@@ -512,7 +517,7 @@ __device__ __forceinline__ float reduce_scatter10(const float v[10], int lane, i
     return y;
 }
 
-// float offset in GGrad of reduced value index: du dv dA dB dC dop dr dg db dz
+// float offset in GGrad of reduced value index: five moments, dop, dr dg db, dz
 __device__ __forceinline__ int grad_offset(int idx) { return idx < 6 ? idx : (idx < 9 ? idx + 2 : 6); }
 
 template <int TW, int TH, int BM>
@@ -548,36 +553,38 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
         const size_t HW = (size_t)V.W * V.H;
         const float fpx = (float)bp.px;
 
-        float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT];
-        float S0[PPT], S1[PPT], S2[PPT], SD[PPT], SA[PPT];
+        // Per pixel: T, the upstream gradients, and Q = sum over the colour, depth
+        // and visibility channels x of g_x S_x, where S_x is the normalised sum of
+        // what is composited behind the current Gaussian.  dL/dalpha_i only ever
+        // needs that dot product, so one running scalar replaces the five sums:
+        // dL/dalpha_i = T_i (cg_i - Q), Q <- alpha_i cg_i + (1 - alpha_i) Q, with
+        // cg_i = c_i . g_C + z_i g_D + g_V.
+        float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT], Q[PPT];
         int last[PPT];
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int py = bp.py0 + j;
             T[j] = 1.f;
-            gC0[j] = gC1[j] = gC2[j] = gD[j] = gA[j] = 0.f;
-            S0[j] = S1[j] = S2[j] = SD[j] = SA[j] = 0.f;
+            gC0[j] = gC1[j] = gC2[j] = gD[j] = gA[j] = Q[j] = 0.f;
             last[j] = 0;
             if (bp.px < V.W && py < V.H) {
                 const size_t p = (size_t)py * V.W + bp.px;
                 last[j] = n_contrib[V.pix_base + p];
-                if (nch <= 1) {
-                    T[j] = final_T[V.pix_base + p];
-                } else if (k * (uint32_t)cp.L < (uint32_t)last[j]) {
-                    const uint32_t slot = cp.part_base[gt] + k;
-                    const int lp = bp.lp0 + j * TW;
-                    S0[j] = slot_field(cp, slot, 0, Gm::TPX)[lp];
-                    S1[j] = slot_field(cp, slot, 1, Gm::TPX)[lp];
-                    S2[j] = slot_field(cp, slot, 2, Gm::TPX)[lp];
-                    SD[j] = slot_field(cp, slot, 3, Gm::TPX)[lp];
-                    SA[j] = slot_field(cp, slot, 4, Gm::TPX)[lp];
-                    T[j] = slot_field(cp, slot, 5, Gm::TPX)[lp];
-                }
                 gC0[j] = G.d_rgb[vi][p];
                 gC1[j] = G.d_rgb[vi][HW + p];
                 gC2[j] = G.d_rgb[vi][2 * HW + p];
                 gD[j] = G.d_depth[vi] ? G.d_depth[vi][p] : 0.f;
                 gA[j] = G.d_alpha[vi] ? G.d_alpha[vi][p] : 0.f;
+                if (nch <= 1) {
+                    T[j] = final_T[V.pix_base + p];
+                } else if (k * (uint32_t)cp.L < (uint32_t)last[j]) {
+                    const uint32_t slot = cp.part_base[gt] + k;
+                    const int lp = bp.lp0 + j * TW;
+                    Q[j] = slot_field(cp, slot, 0, Gm::TPX)[lp] * gC0[j] + slot_field(cp, slot, 1, Gm::TPX)[lp] * gC1[j] +
+                           slot_field(cp, slot, 2, Gm::TPX)[lp] * gC2[j] + slot_field(cp, slot, 3, Gm::TPX)[lp] * gD[j] +
+                           slot_field(cp, slot, 4, Gm::TPX)[lp] * gA[j];
+                    T[j] = slot_field(cp, slot, 5, Gm::TPX)[lp];
+                }
             }
         }
         const int warp_last = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
@@ -593,6 +600,9 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 const float4 c = sm.C[q];
                 const int pos = sm.Pos[q];
                 const float dx = a.x - fpx;
+                // v: sums over the lane's pixels of dp dx, dp dy, dp dx^2, dp dx dy,
+                // dp dy^2 (dp = dL/dpower), dL/do, and w g_R, w g_G, w g_B, w g_D;
+                // the conic is applied per Gaussian in the chain rule that follows
                 float v[NACC];
 #pragma unroll
                 for (int m = 0; m < NACC; ++m) v[m] = 0.f;
@@ -608,28 +618,24 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                     const float alpha = fminf(kAlphaMax, oG);
                     if (alpha < kAlphaMin) continue;
                     any = true;
-                    const float one_m = 1.f - alpha;
-                    T[j] = __fdividef(T[j], one_m);
+                    T[j] = __fdividef(T[j], 1.f - alpha);
                     const float wgt = alpha * T[j];
-                    const float dLda = T[j] * ((c.x - S0[j]) * gC0[j] + (c.y - S1[j]) * gC1[j] +
-                                               (c.z - S2[j]) * gC2[j] + (b.z - SD[j]) * gD[j] + (1.f - SA[j]) * gA[j]);
-                    S0[j] = fmaf(alpha, c.x - S0[j], S0[j]);
-                    S1[j] = fmaf(alpha, c.y - S1[j], S1[j]);
-                    S2[j] = fmaf(alpha, c.z - S2[j], S2[j]);
-                    SD[j] = fmaf(alpha, b.z - SD[j], SD[j]);
-                    SA[j] = fmaf(alpha, 1.f - SA[j], SA[j]);
+                    const float cg = fmaf(c.x, gC0[j], fmaf(c.y, gC1[j], fmaf(c.z, gC2[j], fmaf(b.z, gD[j], gA[j]))));
+                    const float dLda = T[j] * (cg - Q[j]);
+                    Q[j] = fmaf(alpha, cg - Q[j], Q[j]);
                     v[6] = fmaf(wgt, gC0[j], v[6]);
                     v[7] = fmaf(wgt, gC1[j], v[7]);
                     v[8] = fmaf(wgt, gC2[j], v[8]);
                     v[9] = fmaf(wgt, gD[j], v[9]);
                     if (oG < kAlphaMax) {
-                        const float dpow = dLda * alpha;
+                        const float dp = dLda * alpha;
+                        const float dpx = dp * dx, dpy = dp * dy;
                         v[5] = fmaf(dLda, G_, v[5]);
-                        v[0] -= dpow * (a.z * dx + a.w * dy);
-                        v[1] -= dpow * (b.x * dy + a.w * dx);
-                        v[2] -= 0.5f * dpow * dx * dx;
-                        v[3] -= dpow * dx * dy;
-                        v[4] -= 0.5f * dpow * dy * dy;
+                        v[0] += dpx;
+                        v[1] += dpy;
+                        v[2] = fmaf(dpx, dx, v[2]);
+                        v[3] = fmaf(dpx, dy, v[3]);
+                        v[4] = fmaf(dpy, dy, v[4]);
                     }
                 }
                 if (__any_sync(0xffffffffu, any)) {

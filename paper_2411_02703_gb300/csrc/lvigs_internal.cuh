@@ -68,8 +68,13 @@ struct __align__(16) GRec {
     float4 a, b, c;
 };
 
-// Screen-space gradient of one (view, Gaussian): g0 = (du, dv, dA, dB),
-// g1 = (dC, dopacity, dz, -), g2 = (dr, dg, db, -).
+// Screen-space gradient sums of one (view, Gaussian) over its pixels, with
+// dp = dL/dpower and (dx, dy) = (u - px, v - py):
+// g0 = (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy),
+// g1 = (sum dp dy^2, dL/dopacity, dL/dz, -), g2 = (dL/dr, dL/dg, dL/db, -).
+// Since power = -(A dx^2 + C dy^2)/2 - B dx dy, the conic gradients follow per
+// Gaussian: dL/du = -(A m_x + B m_y), dL/dv = -(C m_y + B m_x),
+// dL/dA = -m_xx / 2, dL/dB = -m_xy, dL/dC = -m_yy / 2.
 struct __align__(16) GGrad {
     float4 g0, g1, g2;
 };

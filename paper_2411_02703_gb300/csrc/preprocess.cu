@@ -370,10 +370,10 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         const size_t o = (size_t)vi * N + g;
         if (tiles[o] == 0) continue;
         const GGrad gg = g2d[o];
-        const float du = gg.g0.x, dv = gg.g0.y, dA = gg.g0.z, dB = gg.g0.w;
-        const float dC = gg.g1.x, dop = gg.g1.y, ddepth = gg.g1.z;
+        const float mx_ = gg.g0.x, my_ = gg.g0.y, mxx = gg.g0.z, mxy = gg.g0.w;
+        const float myy = gg.g1.x, dop = gg.g1.y, ddepth = gg.g1.z;
         const float drgb[3] = {gg.g2.x, gg.g2.y, gg.g2.z};
-        if (du == 0.f && dv == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && dop == 0.f &&
+        if (mx_ == 0.f && my_ == 0.f && mxx == 0.f && mxy == 0.f && myy == 0.f && dop == 0.f &&
             ddepth == 0.f && drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f)
             continue;
         any = true;
@@ -406,6 +406,11 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         const float c = T[1][0] * ST[1][0] + T[1][1] * ST[1][1] + T[1][2] * ST[1][2] + 0.3f;
         const float det = a * c - b * b;
         const float id = 1.f / det, id2 = id * id;
+        // screen-space gradients from the compositing moments (power =
+        // -(A dx^2 + C dy^2)/2 - B dx dy with the conic (A, B, C) = (c, -b, a) / det)
+        const float cA = c * id, cB = -b * id, cC = a * id;
+        const float du = -(cA * mx_ + cB * my_), dv = -(cC * my_ + cB * mx_);
+        const float dA = -0.5f * mxx, dB = -mxy, dC = -0.5f * myy;
         // conic (A, B, C) = (c, -b, a) / det
         const float da = -c * c * id2 * dA + b * c * id2 * dB + (id - a * c * id2) * dC;
         const float dc = (id - a * c * id2) * dA + a * b * id2 * dB - a * a * id2 * dC;
