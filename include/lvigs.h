@@ -165,6 +165,42 @@ lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
                         float lambda_ssim, float lambda_depth, double *loss_out, float *d_rgb,
                         float *d_depth, void *stream);
 
+/* lvigs_loss for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the loss above.
+ *
+ * Who cannot allocate: a host whose allocator already owns the device-memory
+ * budget (a caching allocator holding the free memory, an embedded process
+ * with a fixed memory plan), and a real-time loop such as the tracking thread
+ * of a SLAM front end, where cudaMalloc / cudaFree are off limits because
+ * cudaFree synchronises the whole device.  lvigs_loss grows its workspace in a
+ * context with cudaMalloc; this entry point takes no context and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Its scratch is a fixed 12 MiB array inside the library's device code, held
+ * by every GPU that loads the library until the process exits.  Images are
+ * limited to LVIGS_LOSS_NOALLOC_MAX_PIXELS pixels (640 x 512) and
+ * LVIGS_LOSS_NOALLOC_MAX_SIDE pixels per side; larger ones return
+ * LVIGS_ERR_CAPACITY before anything is enqueued.
+ *
+ * Arguments, layouts and results are those of lvigs_loss, on the current
+ * device (`stream` must belong to it).  LVIGS_ERR_INVALID_ARG for the argument
+ * errors of lvigs_loss; LVIGS_ERR_CUDA when a CUDA call fails.
+ *
+ * Set-up: the first call on a device looks up the device address of the
+ * scratch array (which may load the library's module onto that device), so
+ * make that first call before any stream capture begins.
+ *
+ * Every call on a device shares the one array, and it keeps what the last
+ * call left (no call depends on it: each writes everything it reads).  Calls
+ * that overlap on the GPU (other streams, other host threads) race on it:
+ * order them, for example on one stream. */
+#define LVIGS_LOSS_NOALLOC_MAX_PIXELS 327680
+#define LVIGS_LOSS_NOALLOC_MAX_SIDE 2048
+lvigs_status lvigs_loss_noalloc(int width, int height, const float *rgb, const float *depth,
+                                const float *gt_rgb, const float *lidar_depth, float lambda_ssim,
+                                float lambda_depth, double *loss_out, float *d_rgb, float *d_depth,
+                                void *stream);
+
 /* One pyramid level down (Sec. III-D): rgb 2x2 box mean, depth the mean of
  * the valid (> 0) samples of each 2x2 block (0 if none).  Output size is
  * (width/2) x (height/2). */

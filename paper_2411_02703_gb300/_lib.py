@@ -75,6 +75,7 @@ SIGNATURES = {
                           ctypes.POINTER(_I), _P]),
     "lvigs_backward": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(Grads), _P]),
     "lvigs_loss": (_I, [_P, _I, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
+    "lvigs_loss_noalloc": (_I, [_I, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
     "lvigs_pyramid_down": (_I, [_I, _I, _P, _P, _P, _P, _P]),
     "lvigs_train_step_batched": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Batch), ctypes.POINTER(Grads), _P]),
     "lvigs_debug_keys": (_I, [_P, _I, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),

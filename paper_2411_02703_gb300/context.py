@@ -59,6 +59,37 @@ def level_size(cam, level):
     return int(cam.W) >> level, int(cam.H) >> level
 
 
+LOSS_NOALLOC_MAX_PIXELS = 640 * 512
+LOSS_NOALLOC_MAX_SIDE = 2048
+
+
+def loss_noalloc(rgb, depth, gt, lidar, lambda_ssim, lambda_depth, terms, d_rgb=None, d_depth=None):
+    """The mapping loss through lvigs_loss_noalloc, for callers that cannot let
+    the library allocate device memory (their allocator owns the budget, or a
+    real-time loop where cudaFree would synchronise the device).  Every output
+    is a caller-provided tensor: `terms` float64 [4], `d_rgb` [3,H,W] and
+    `d_depth` [H,W] (either may be None).  The library's scratch is a fixed
+    array on the device, shared by all calls: calls that overlap on the GPU
+    race, so order them (for example on one stream)."""
+    _check_tensor(rgb, "rgb")
+    _check_tensor(gt, "gt", rgb.shape)
+    H, W = rgb.shape[1], rgb.shape[2]
+    for t, name, shape in ((depth, "depth", (H, W)), (lidar, "lidar", (H, W)), (d_rgb, "d_rgb", rgb.shape),
+                           (d_depth, "d_depth", (H, W))):
+        if t is not None:
+            _check_tensor(t, name, shape)
+    if not (terms.is_cuda and terms.dtype == torch.float64 and terms.numel() >= 4 and terms.is_contiguous()):
+        raise ValueError("terms must be a contiguous CUDA float64 tensor of 4 elements")
+    code = L.load().lvigs_loss_noalloc(W, H, _ptr(rgb), _ptr(depth), _ptr(gt), _ptr(lidar), float(lambda_ssim),
+                                       float(lambda_depth), _ptr(terms), _ptr(d_rgb), _ptr(d_depth), _stream())
+    if code == 4:
+        raise L.LvigsError(code, "lvigs_loss_noalloc",
+                           f"{W}x{H} image beyond the fixed scratch: at most {LOSS_NOALLOC_MAX_PIXELS} pixels "
+                           f"and {LOSS_NOALLOC_MAX_SIDE} per side")
+    L.check(code, "lvigs_loss_noalloc")
+    return terms, d_rgb, d_depth
+
+
 class Context:
     """One library context (workspace, view slots, batched-step graph)."""
 
