@@ -199,6 +199,22 @@ def lidar_scene(n, seed=BASE_SEED + 2, sh_degree=3, log_scale=(-3.0, 0.5)):
     return params, phase
 
 
+def fresh_scan(n, step, seed=BASE_SEED + 2):
+    """Colourised points of one new LiDAR sweep of the ``lidar_scene`` world (the
+    same ground and facades), taken at a seeded trajectory position for map
+    expansion step ``step``: at most n points, in acquisition order, with their
+    procedural colours in [0, 1].  Returns float32 (points [k,3], colours [k,3])."""
+    rng = _rng(seed)
+    lo, hi = _boxes(rng)
+    phase = float(rng.uniform(0, 2 * math.pi))
+    r2 = _rng(seed + 1000 + int(step))
+    origin, _ = trajectory_pose(float(r2.uniform(0.05, 0.95)), phase)
+    P = lidar_sweep(origin, lo, hi)
+    if P.shape[0] > n:
+        P = P[np.sort(r2.choice(P.shape[0], size=n, replace=False))]
+    return P.astype(np.float32), _texture(P).astype(np.float32)
+
+
 def trajectory_cameras(n_views, seed=BASE_SEED + 3, phase=0.0, W=1280, H=1024, f=860.0):
     """Keyframe cameras at seeded positions along the trajectory."""
     rng = _rng(seed)
