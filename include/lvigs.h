@@ -273,6 +273,91 @@ lvigs_status lvigs_profile_enable(lvigs_ctx *ctx, int enable);
  * kernel launches per replay of the batched-step graph, then resets. */
 lvigs_status lvigs_profile_read(lvigs_ctx *ctx, double *ms, int64_t *calls, int *kernels_per_step);
 
+/* ----------------------------------------------------------------------- */
+/* Map maintenance around the differentiable path: the optimiser step, map  */
+/* expansion from colourised LiDAR points and pruning (Sec. III-C, III-E).  */
+/* ----------------------------------------------------------------------- */
+
+/* Five parameter-shaped device buffers (caller-owned, mutable) in the layouts
+ * of lvigs_gaussians; rows beyond the live count are capacity. */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+} lvigs_param_buffers;
+
+/* Optimiser of the Gaussian parameters.  Sec. III-E names the parameters
+ * (position, rotation, scaling, density, SH colour) and the loss but not the
+ * optimiser; Adam with per-parameter learning rates is the reading taken.
+ * Defaults: lr means 1.6e-4, log-scales 5e-3, quaternions 1e-3, opacity
+ * 5e-2, SH band 0 2.5e-3, higher SH bands 1.25e-4; beta1 0.9, beta2 0.999,
+ * eps 1e-15. */
+typedef struct {
+    float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
+    double beta1, beta2, eps; /* double: 1 - beta is formed before rounding to binary32 */
+} lvigs_adam_config;
+
+void lvigs_adam_config_default(lvigs_adam_config *cfg);
+
+/* One Adam step over rows [0, n) of every parameter, in one launch:
+ *   m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+ *   p <- p - lr / (1 - b1^t) * m / (sqrt(v) / sqrt(1 - b2^t) + eps),
+ * with t = `step` >= 1 the step count after this update.  exp_avg and
+ * exp_avg_sq hold m and v (zero before the first step).  zero_grads = 1 also
+ * clears the gradient buffers (grads->accumulate is ignored).  cfg may be
+ * NULL (defaults).  LVIGS_ERR_INVALID_ARG on a NULL buffer with n > 0, n < 0,
+ * sh_stride_k < 1, step < 1 or betas outside [0, 1). */
+lvigs_status lvigs_adam_step(const lvigs_param_buffers *params, const lvigs_grads *grads,
+                             const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq,
+                             int64_t n, int sh_stride_k, int64_t step, const lvigs_adam_config *cfg,
+                             int zero_grads, void *stream);
+
+/* Initialisation of new Gaussians (Sec. III-E) and the filter on Gaussian
+ * additions (Sec. III-C). */
+typedef struct {
+    float init_opacity;  /* opacity of a new Gaussian (stored as its logit): 0.1 */
+    float min_dist2;     /* floor of the mean squared neighbour distance: 1e-7 */
+    float tau_alpha;     /* filter threshold tau_alpha: 0.5 */
+    int filter_literal;  /* 0 (default): drop a point whose pixel has transparency
+                            1 - V_p <= tau_alpha (the map is already opaque there);
+                            1: drop when V_p <= tau_alpha, the inequality as printed */
+} lvigs_init_config;
+
+void lvigs_init_config_default(lvigs_init_config *cfg);
+
+/* Map expansion: Gaussians for k colourised LiDAR points (device float
+ * points [k,3], colours [k,3] in [0,1]) are written at rows
+ * [n, n + k_kept) of `params`, in the points' order:
+ *   centre = the point; log-scale (all three axes) = 0.5 ln(max(d2, min_dist2))
+ *   with d2 the mean squared distance to the 3 nearest other kept points
+ *   (fewer if there are fewer; 0 if none); quaternion (1,0,0,0); opacity
+ *   logit = ln(o / (1 - o)); SH band 0 = (colour - 0.5) / Y_00 with
+ *   Y_00 = 1 / (2 sqrt(pi)), higher bands 0.
+ * Filter (when alpha != NULL): each point is projected into `cam` at pyramid
+ * level `level` in binary32, one rounding per operation in the order
+ * x_c = ((R00 x + R01 y) + R02 z) + t0 (likewise y_c, z_c), u = (fx x_c)/z_c
+ * + cx, px = floor(u + 0.5) (likewise v, py); a point with z_c > 0.2 inside
+ * the image is dropped per cfg->filter_literal against alpha[py, px] (the
+ * V_p image of Eq. (5) at that level, [H_l, W_l]); other points are kept.
+ * exp_avg / exp_avg_sq (either may be NULL) get zero rows.  Every buffer must
+ * have `capacity` rows; LVIGS_ERR_CAPACITY if n + k > capacity (checked
+ * before any work).  *n_out receives n + k_kept; the call waits on `stream`.
+ * cfg may be NULL (defaults).  Uses the context's workspace. */
+lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const float *colours, int64_t k,
+                                    const lvigs_camera *cam, int level, const float *alpha,
+                                    const lvigs_init_config *cfg, const lvigs_param_buffers *params,
+                                    const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq,
+                                    int64_t n, int64_t capacity, int sh_stride_k, int64_t *n_out, void *stream);
+
+/* Pruning (the prunable opacity of Sec. III-C): rows [0, n) whose opacity
+ * sigmoid(logit) is below min_opacity are removed from `params` and the Adam
+ * state (either may be NULL), keeping the order of the rest.  The test is
+ * logit >= (float)ln(m / (1 - m)), computed in double and rounded once.
+ * Gradient buffers are not touched: the next backward should overwrite them
+ * (accumulate = 0).  *n_out receives the count kept; the call waits on
+ * `stream`.  min_opacity in (0, 1). */
+lvigs_status lvigs_prune_gaussians(lvigs_ctx *ctx, float min_opacity, const lvigs_param_buffers *params,
+                                   const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq,
+                                   int64_t n, int sh_stride_k, int64_t *n_out, void *stream);
+
 /* Work counts of the last batched step (waits on `stream`): out[0] visible
  * (view, Gaussian) pairs, out[1] (tile, Gaussian) instances, out[2] the sum
  * over pixels of the contributor counts, out[3] pixels rendered. */

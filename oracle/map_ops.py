@@ -60,6 +60,8 @@ def adam_step(params, grads, exp_avg, exp_avg_sq, step, cfg=None):
     bc2 = 1.0 - b2 ** step
     P, M, V = {}, {}, {}
     for k in PARAM_KEYS:
+        if k not in params:
+            continue
         g = np.asarray(grads[k], np.float64)
         m = b1 * np.asarray(exp_avg[k], np.float64) + (1.0 - b1) * g
         v = b2 * np.asarray(exp_avg_sq[k], np.float64) + (1.0 - b2) * g * g

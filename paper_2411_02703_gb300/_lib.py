@@ -62,6 +62,22 @@ class Batch(ctypes.Structure):
                 ("alpha_out", ctypes.POINTER(ctypes.c_void_p))]
 
 
+class ParamBuffers(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class AdamConfig(ctypes.Structure):
+    _fields_ = ([(n, ctypes.c_float) for n in ("lr_means", "lr_log_scales", "lr_quats", "lr_opacity", "lr_sh_dc",
+                                               "lr_sh_rest")]
+                + [(n, ctypes.c_double) for n in ("beta1", "beta2", "eps")])
+
+
+class InitConfig(ctypes.Structure):
+    _fields_ = [("init_opacity", ctypes.c_float), ("min_dist2", ctypes.c_float), ("tau_alpha", ctypes.c_float),
+                ("filter_literal", ctypes.c_int)]
+
+
 # every entry point declared in include/lvigs.h, with its ctypes signature
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -86,6 +102,18 @@ SIGNATURES = {
     "lvigs_step_stats": (_I, [_P, ctypes.POINTER(ctypes.c_int64), _P]),
     "lvigs_autotune_batched": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Batch), ctypes.POINTER(Grads), _I,
                                     _P, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double)]),
+    "lvigs_adam_config_default": (None, [ctypes.POINTER(AdamConfig)]),
+    "lvigs_adam_step": (_I, [ctypes.POINTER(ParamBuffers), ctypes.POINTER(Grads), ctypes.POINTER(ParamBuffers),
+                             ctypes.POINTER(ParamBuffers), ctypes.c_int64, _I, ctypes.c_int64,
+                             ctypes.POINTER(AdamConfig), _I, _P]),
+    "lvigs_init_config_default": (None, [ctypes.POINTER(InitConfig)]),
+    "lvigs_append_gaussians": (_I, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(Camera), _I, _P,
+                                    ctypes.POINTER(InitConfig), ctypes.POINTER(ParamBuffers),
+                                    ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers), ctypes.c_int64,
+                                    ctypes.c_int64, _I, ctypes.POINTER(ctypes.c_int64), _P]),
+    "lvigs_prune_gaussians": (_I, [_P, ctypes.c_float, ctypes.POINTER(ParamBuffers), ctypes.POINTER(ParamBuffers),
+                                   ctypes.POINTER(ParamBuffers), ctypes.c_int64, _I,
+                                   ctypes.POINTER(ctypes.c_int64), _P]),
     "lvigs_profile_enable": (_I, [_P, _I]),
     "lvigs_profile_read": (_I, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                 ctypes.POINTER(_I)]),

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "composite.cu", "loss.cu", "loss_noalloc.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "composite.cu", "loss.cu", "loss_noalloc.cu", "map.cu"]
 
 
 def _nvcc() -> str:

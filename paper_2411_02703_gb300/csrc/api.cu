@@ -5,6 +5,7 @@
 // Host arithmetic that feeds the tile keys (the pyramid-level intrinsics and
 // the Jacobian clamp limits) is plain binary32 C++ compiled with
 // -ffp-contract=off, one rounding per operation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -101,6 +102,11 @@ struct lvigs_ctx {
     BatchKey graph_key;
     bool graph_ok = false;
     int kernels_per_step = 0;
+
+    // map maintenance (append / prune) scratch, kept apart from the step's
+    // buffers so that growing it does not invalidate the step's graph
+    DevBuf mp_pts, mp_col, mp_keep, mp_offs, mp_keys, mp_vals, mp_keys2, mp_vals2, mp_scan, mp_radix, mp_cells,
+        mp_logs, mp_small, mp_tmp;
 
     // opt-in per-phase device timing of eagerly enqueued work
     bool prof = false;
@@ -499,7 +505,10 @@ void lvigs_destroy(lvigs_ctx *ctx) {
     release_state(ctx, ctx->batch);
     DevBuf *shared[] = {&ctx->pos, &ctx->ck, &ctx->cv, &ctx->ck2, &ctx->cv2, &ctx->scan_tmp, &ctx->radix_tmp,
                         &ctx->status, &ctx->g2d, &ctx->loss_tmp, &ctx->stats, &ctx->img_rgb, &ctx->img_depth,
-                        &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->losses_dev};
+                        &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->losses_dev, &ctx->mp_pts,
+                        &ctx->mp_col, &ctx->mp_keep, &ctx->mp_offs, &ctx->mp_keys, &ctx->mp_vals, &ctx->mp_keys2,
+                        &ctx->mp_vals2, &ctx->mp_scan, &ctx->mp_radix, &ctx->mp_cells, &ctx->mp_logs,
+                        &ctx->mp_small, &ctx->mp_tmp};
     for (DevBuf *b : shared) release(ctx, *b);
     for (int v = 0; v < kMaxViews; ++v) {
         release(ctx, ctx->gt_stage[v]);
@@ -1104,5 +1113,275 @@ extern "C" lvigs_status lvigs_autotune_batched(lvigs_ctx *ctx, const lvigs_gauss
     ctx->step_pending = false;
     // view slots rendered with another tile size stay valid (they keep their own view set)
     if (chosen) *chosen = ctx->cfg;
+    return LVIGS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Map maintenance: Adam, expansion from colourised LiDAR points, pruning.
+// ---------------------------------------------------------------------------
+
+void lvigs_adam_config_default(lvigs_adam_config *c) {
+    if (!c) return;
+    c->lr_means = 1.6e-4f;
+    c->lr_log_scales = 5e-3f;
+    c->lr_quats = 1e-3f;
+    c->lr_opacity = 5e-2f;
+    c->lr_sh_dc = 2.5e-3f;
+    c->lr_sh_rest = 2.5e-3f / 20.0f;
+    c->beta1 = 0.9;
+    c->beta2 = 0.999;
+    c->eps = 1e-15;
+}
+
+namespace {
+
+bool bufs_complete(const lvigs_param_buffers *b) {
+    return b && b->means && b->log_scales && b->quats && b->opacity_logits && b->sh;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+} // namespace
+
+lvigs_status lvigs_adam_step(const lvigs_param_buffers *params, const lvigs_grads *grads,
+                             const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq, int64_t n,
+                             int sh_stride_k, int64_t step, const lvigs_adam_config *cfg_in, int zero_grads,
+                             void *stream) {
+    if (n < 0 || sh_stride_k < 1 || step < 1) return LVIGS_ERR_INVALID_ARG;
+    lvigs_adam_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else lvigs_adam_config_default(&cfg);
+    if (!(cfg.beta1 >= 0.0 && cfg.beta1 < 1.0) || !(cfg.beta2 >= 0.0 && cfg.beta2 < 1.0) || !(cfg.eps >= 0.0))
+        return LVIGS_ERR_INVALID_ARG;
+    if (n == 0) return LVIGS_OK;
+    if (!bufs_complete(params) || !bufs_complete(exp_avg) || !bufs_complete(exp_avg_sq) || !grads ||
+        !grads->d_means || !grads->d_log_scales || !grads->d_quats || !grads->d_opacity_logits || !grads->d_sh)
+        return LVIGS_ERR_INVALID_ARG;
+    AdamArgs A{};
+    float *P[5] = {params->means, params->log_scales, params->quats, params->opacity_logits, params->sh};
+    float *G[5] = {grads->d_means, grads->d_log_scales, grads->d_quats, grads->d_opacity_logits, grads->d_sh};
+    float *M[5] = {exp_avg->means, exp_avg->log_scales, exp_avg->quats, exp_avg->opacity_logits, exp_avg->sh};
+    float *V[5] = {exp_avg_sq->means, exp_avg_sq->log_scales, exp_avg_sq->quats, exp_avg_sq->opacity_logits,
+                   exp_avg_sq->sh};
+    const int64_t width[5] = {3, 3, 4, 1, 3 * (int64_t)sh_stride_k};
+    const float lr[5] = {cfg.lr_means, cfg.lr_log_scales, cfg.lr_quats, cfg.lr_opacity, cfg.lr_sh_dc};
+    A.unit_base[0] = 0;
+    for (int s = 0; s < kAdamSegs; ++s) {
+        AdamSeg &S = A.seg[s];
+        S.p = P[s];
+        S.g = G[s];
+        S.m = M[s];
+        S.v = V[s];
+        S.len = n * width[s];
+        S.lr = lr[s];
+        S.lr_rest = s == 4 ? cfg.lr_sh_rest : lr[s];
+        S.sh_k = s == 4 ? sh_stride_k : 0;
+        S.vec = aligned16(S.p) && aligned16(S.g) && aligned16(S.m) && aligned16(S.v);
+        A.unit_base[s + 1] = A.unit_base[s] + (S.len + 3) / 4;
+    }
+    A.b1 = (float)cfg.beta1;
+    A.b2 = (float)cfg.beta2;
+    A.omb1 = (float)(1.0 - cfg.beta1);
+    A.omb2 = (float)(1.0 - cfg.beta2);
+    A.eps = (float)cfg.eps;
+    A.inv_bc1 = (float)(1.0 / (1.0 - std::pow(cfg.beta1, (double)step)));
+    A.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow(cfg.beta2, (double)step)));
+    A.zero_grads = zero_grads ? 1 : 0;
+    launch_adam(A, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? LVIGS_OK : LVIGS_ERR_CUDA;
+}
+
+void lvigs_init_config_default(lvigs_init_config *c) {
+    if (!c) return;
+    c->init_opacity = 0.1f;
+    c->min_dist2 = 1e-7f;
+    c->tau_alpha = 0.5f;
+    c->filter_literal = 0;
+}
+
+namespace {
+
+// Uniform grid for k points in the box [lo, hi]: about one point per cell of
+// the box's volume, at most 16384 cells per axis (so the binary32 cell
+// coordinates stay within 1% of a cell of exact) and 2^24 cells in total.
+KnnGrid make_grid(const float lo[3], const float hi[3], int64_t k) {
+    double ext[3], emax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        ext[a] = (double)hi[a] - (double)lo[a];
+        emax = std::max(emax, ext[a]);
+    }
+    const double floor_ext = std::max(emax * 1e-3, 1e-6);
+    double vol = 1.0;
+    for (int a = 0; a < 3; ++a) vol *= std::max(ext[a], floor_ext);
+    double h = std::cbrt(vol / (double)std::max<int64_t>(k, 1));
+    h = std::max(h, std::max(emax / 16000.0, 1e-6));
+    KnnGrid G{};
+    for (;;) {
+        double cells = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            G.D[a] = (int)std::floor(ext[a] / h) + 1;
+            cells *= G.D[a];
+        }
+        if (cells <= (double)(1 << 24) && G.D[0] <= 16384 && G.D[1] <= 16384 && G.D[2] <= 16384) break;
+        h *= 1.25;
+    }
+    for (int a = 0; a < 3; ++a) G.o[a] = lo[a];
+    G.h = (float)h;
+    G.inv_h = (float)(1.0 / h);
+    return G;
+}
+
+} // namespace
+
+lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const float *colours, int64_t k,
+                                    const lvigs_camera *cam, int level, const float *alpha,
+                                    const lvigs_init_config *cfg_in, const lvigs_param_buffers *params,
+                                    const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq,
+                                    int64_t n, int64_t capacity, int sh_stride_k, int64_t *n_out, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    if (!n_out || n < 0 || k < 0 || sh_stride_k < 1 || capacity < 0)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad append arguments");
+    if (k > 0 && (!points || !colours)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "points / colours are NULL");
+    if (!bufs_complete(params)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL parameter buffer");
+    if ((exp_avg && !bufs_complete(exp_avg)) || (exp_avg_sq && !bufs_complete(exp_avg_sq)))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "incomplete Adam state buffers");
+    if (n + k > capacity) return fail(ctx, LVIGS_ERR_CAPACITY, "n + k exceeds the parameter capacity");
+    if (k >= ((int64_t)1 << 31) || n + k >= ((int64_t)1 << 31))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "too many Gaussians");
+    lvigs_init_config cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else lvigs_init_config_default(&cfg);
+    if (!(cfg.init_opacity > 0.f && cfg.init_opacity < 1.f) || !(cfg.min_dist2 > 0.f))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "init_opacity must be in (0,1) and min_dist2 > 0");
+    if (alpha) LV_TRY(check_camera(ctx, cam, level));
+    cudaStream_t s = (cudaStream_t)stream;
+    *n_out = n;
+    if (k == 0) return LVIGS_OK;
+
+    const float *src_pts = points, *src_col = colours;
+    int64_t kk = k;
+    LV_TRY(ensure(ctx, ctx->mp_small, 64));
+    uint32_t *small = (uint32_t *)ctx->mp_small.p; // [0] count, [2..8) box
+    if (alpha) {
+        const ViewDesc v = make_view(*cam, level, 16, 16);
+        PointCamera C{};
+        for (int i = 0; i < 9; ++i) C.R[i] = v.R[i];
+        for (int i = 0; i < 3; ++i) C.t[i] = v.t[i];
+        C.fx = v.fx;
+        C.fy = v.fy;
+        C.cx = v.cx;
+        C.cy = v.cy;
+        C.W = v.W;
+        C.H = v.H;
+        C.near = 0.2f;
+        LV_TRY(ensure(ctx, ctx->mp_keep, (size_t)k * 4));
+        LV_TRY(ensure(ctx, ctx->mp_offs, (size_t)(k + 1) * 4));
+        LV_TRY(ensure(ctx, ctx->mp_scan, scan_tmp_words(k) * 4));
+        LV_TRY(ensure(ctx, ctx->mp_pts, (size_t)k * 12));
+        LV_TRY(ensure(ctx, ctx->mp_col, (size_t)k * 12));
+        uint32_t *keep = (uint32_t *)ctx->mp_keep.p, *offs = (uint32_t *)ctx->mp_offs.p;
+        launch_point_filter(points, k, C, alpha, cfg.tau_alpha, cfg.filter_literal, keep, s);
+        launch_scan(keep, nullptr, 1, offs, offs + k, nullptr, k, (uint32_t *)ctx->mp_scan.p, s);
+        launch_gather_points(points, colours, k, keep, offs, (float *)ctx->mp_pts.p, (float *)ctx->mp_col.p, s);
+        LV_CUDA(cudaMemcpyAsync(ctx->host_counters, offs + k, 4, cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        kk = ctx->host_counters[0];
+        src_pts = (const float *)ctx->mp_pts.p;
+        src_col = (const float *)ctx->mp_col.p;
+        if (kk == 0) return LVIGS_OK;
+    }
+
+    // bounding box -> grid
+    int *box = (int *)(small + 2);
+    launch_bbox(src_pts, kk, box, s);
+    int hbox[6];
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, box, 16, cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(hbox, ctx->host_counters, 16);
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, box + 4, 8, cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(hbox + 4, ctx->host_counters, 8);
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = ord_to_float(hbox[a]);
+        hi[a] = ord_to_float(hbox[3 + a]);
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]))
+            return fail(ctx, LVIGS_ERR_INVALID_ARG, "non-finite point coordinates");
+    }
+    const KnnGrid G = make_grid(lo, hi, kk);
+    const uint32_t n_cells = (uint32_t)G.D[0] * (uint32_t)G.D[1] * (uint32_t)G.D[2];
+    int bits = 1;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)n_cells) ++bits;
+
+    LV_TRY(ensure(ctx, ctx->mp_keys, (size_t)kk * 4));
+    LV_TRY(ensure(ctx, ctx->mp_vals, (size_t)kk * 4));
+    LV_TRY(ensure(ctx, ctx->mp_keys2, (size_t)kk * 4));
+    LV_TRY(ensure(ctx, ctx->mp_vals2, (size_t)kk * 4));
+    LV_TRY(ensure(ctx, ctx->mp_radix, radix_tmp_words(kk) * 4));
+    LV_TRY(ensure(ctx, ctx->mp_cells, (size_t)n_cells * sizeof(uint2)));
+    LV_TRY(ensure(ctx, ctx->mp_logs, (size_t)kk * 4));
+    uint32_t *keys = (uint32_t *)ctx->mp_keys.p, *vals = (uint32_t *)ctx->mp_vals.p;
+    uint32_t *keys2 = (uint32_t *)ctx->mp_keys2.p, *vals2 = (uint32_t *)ctx->mp_vals2.p;
+    launch_cell_keys(src_pts, kk, G, keys, vals, s);
+    const int alt = launch_radix_sort(keys, vals, keys2, vals2, nullptr, kk, bits, (uint32_t *)ctx->mp_radix.p, s);
+    const uint32_t *skeys = alt ? keys2 : keys, *svals = alt ? vals2 : vals;
+    launch_set_u32(small, (uint32_t)kk, s);
+    launch_ranges(skeys, small, kk, (uint2 *)ctx->mp_cells.p, n_cells, s);
+    launch_knn(src_pts, kk, G, (const uint2 *)ctx->mp_cells.p, svals, cfg.min_dist2, (float *)ctx->mp_logs.p, s);
+
+    const ParamBufs P{params->means, params->log_scales, params->quats, params->opacity_logits, params->sh};
+    ParamBufs Mb{}, Vb{};
+    if (exp_avg) Mb = {exp_avg->means, exp_avg->log_scales, exp_avg->quats, exp_avg->opacity_logits, exp_avg->sh};
+    if (exp_avg_sq)
+        Vb = {exp_avg_sq->means, exp_avg_sq->log_scales, exp_avg_sq->quats, exp_avg_sq->opacity_logits,
+              exp_avg_sq->sh};
+    const double o = (double)cfg.init_opacity;
+    const float logit = (float)std::log(o / (1.0 - o));
+    const float inv_c0 = (float)(2.0 * std::sqrt(3.14159265358979323846));
+    launch_init_rows(src_pts, src_col, (const float *)ctx->mp_logs.p, kk, n, P, Mb, Vb, sh_stride_k, logit, inv_c0, s);
+    LV_CUDA(cudaGetLastError());
+    *n_out = n + kk;
+    return LVIGS_OK;
+}
+
+lvigs_status lvigs_prune_gaussians(lvigs_ctx *ctx, float min_opacity, const lvigs_param_buffers *params,
+                                   const lvigs_param_buffers *exp_avg, const lvigs_param_buffers *exp_avg_sq,
+                                   int64_t n, int sh_stride_k, int64_t *n_out, void *stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    if (!n_out || n < 0 || n >= ((int64_t)1 << 31) || sh_stride_k < 1 || !(min_opacity > 0.f && min_opacity < 1.f))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad prune arguments");
+    if (!bufs_complete(params)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL parameter buffer");
+    if ((exp_avg && !bufs_complete(exp_avg)) || (exp_avg_sq && !bufs_complete(exp_avg_sq)))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "incomplete Adam state buffers");
+    *n_out = n;
+    if (n == 0) return LVIGS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double m = (double)min_opacity;
+    const float thr = (float)std::log(m / (1.0 - m));
+    LV_TRY(ensure(ctx, ctx->mp_keep, (size_t)n * 4));
+    LV_TRY(ensure(ctx, ctx->mp_offs, (size_t)(n + 1) * 4));
+    LV_TRY(ensure(ctx, ctx->mp_scan, scan_tmp_words(n) * 4));
+    uint32_t *keep = (uint32_t *)ctx->mp_keep.p, *offs = (uint32_t *)ctx->mp_offs.p;
+    launch_prune_flags(params->opacity_logits, n, thr, keep, s);
+    launch_scan(keep, nullptr, 1, offs, offs + n, nullptr, n, (uint32_t *)ctx->mp_scan.p, s);
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, offs + n, 4, cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const int64_t kept = ctx->host_counters[0];
+    if (kept == n) return LVIGS_OK;
+    const int widths[5] = {3, 3, 4, 1, 3 * sh_stride_k};
+    LV_TRY(ensure(ctx, ctx->mp_tmp, (size_t)n * widths[4] * 4));
+    float *tmp = (float *)ctx->mp_tmp.p;
+    const lvigs_param_buffers *sets[3] = {params, exp_avg, exp_avg_sq};
+    for (const lvigs_param_buffers *b : sets) {
+        if (!b) continue;
+        float *bufs[5] = {b->means, b->log_scales, b->quats, b->opacity_logits, b->sh};
+        for (int f = 0; f < 5; ++f) {
+            launch_compact_rows(bufs[f], tmp, n, widths[f], keep, offs, s);
+            if (kept > 0)
+                LV_CUDA(cudaMemcpyAsync(bufs[f], tmp, (size_t)kept * widths[f] * 4, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    LV_CUDA(cudaGetLastError());
+    *n_out = kept;
     return LVIGS_OK;
 }

@@ -196,4 +196,59 @@ void launch_loss(const LossViews &lv, void *tmp, cudaStream_t s);
 void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, float *rgb_out,
                          float *depth_out, cudaStream_t s);
 
+// ---- map maintenance (map.cu) ----
+// Five parameter-shaped buffers (layouts of the Gaussian parameters).
+struct ParamBufs {
+    float *means, *log_scales, *quats, *opacity_logits, *sh;
+};
+
+constexpr int kAdamSegs = 5;
+struct AdamSeg {
+    float *p, *g, *m, *v;
+    int64_t len;     // floats
+    float lr, lr_rest; // lr_rest: SH coefficients other than band 0
+    int sh_k;        // coefficients per Gaussian for the SH segment, 0 otherwise
+    int vec;         // all four pointers 16-byte aligned
+};
+struct AdamArgs {
+    AdamSeg seg[kAdamSegs];
+    int64_t unit_base[kAdamSegs + 1]; // prefix of ceil(len / 4)
+    float b1, b2, omb1, omb2, eps; // omb = 1 - b, formed in double
+    float inv_bc1, inv_sqrt_bc2;   // 1 / (1 - b1^t), 1 / sqrt(1 - b2^t)
+    int zero_grads;
+};
+void launch_adam(const AdamArgs &A, cudaStream_t s);
+
+// Level camera for the point filter.
+struct PointCamera {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float near;
+};
+void launch_point_filter(const float *pts, int64_t k, const PointCamera &C, const float *alpha, float tau, int literal,
+                         uint32_t *keep, cudaStream_t s);
+void launch_gather_points(const float *pts, const float *col, int64_t k, const uint32_t *keep, const uint32_t *offs,
+                          float *pts_out, float *col_out, cudaStream_t s);
+// box: 6 ints, ordered-integer images of (min xyz, max xyz); ord_to_float decodes them.
+void launch_bbox(const float *pts, int64_t k, int *box, cudaStream_t s);
+float ord_to_float(int o);
+
+// Uniform grid of the neighbour search: origin o, cell size h, D cells per axis.
+struct KnnGrid {
+    float o[3];
+    float h, inv_h;
+    int D[3];
+};
+void launch_cell_keys(const float *pts, int64_t k, const KnnGrid &G, uint32_t *keys, uint32_t *vals, cudaStream_t s);
+void launch_knn(const float *pts, int64_t k, const KnnGrid &G, const uint2 *cells, const uint32_t *order,
+                float min_dist2, float *log_scales_out, cudaStream_t s);
+void launch_init_rows(const float *pts, const float *col, const float *log_s, int64_t k, int64_t n0,
+                      const ParamBufs &P, const ParamBufs &M, const ParamBufs &V, int K, float opacity_logit,
+                      float inv_c0, cudaStream_t s);
+void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
+void launch_prune_flags(const float *logits, int64_t n, float thr, uint32_t *keep, cudaStream_t s);
+void launch_compact_rows(const float *src, float *dst, int64_t n, int w, const uint32_t *keep, const uint32_t *offs,
+                         cudaStream_t s);
+
 } // namespace lvigs
