@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--batch-depth", type=int, default=0)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-map", action="store_true", help="skip the map-maintenance timings")
     return ap.parse_args()
 
 
@@ -134,13 +135,15 @@ def algorithmic_bytes(N, V, K, n_vis, M, P, loaded, pyr_px=0):
 
 def alu_flops(n_contrib_sum):
     # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernel
-    # source: forward 20 (offset, quadratic form 7, exp 2, alpha 2, transmittance
-    # 2, colour/depth 5, weight 1), backward 55 (the forward's 13 to alpha, the
-    # transmittance division 2, dL/dalpha 11, five suffix sums 10, ten partials
-    # 19).  Evaluations are counted as the sum over pixels of the last
-    # contributor's list position, an upper bound (it includes list entries the
-    # 8x8-block culling skips), so the achieved rate is an upper bound too.
-    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 55.0 * n_contrib_sum}
+    # source (an FMA counts 2): forward 20 (offset, quadratic form 7, exp 2,
+    # alpha 2, transmittance 2, colour/depth 5, weight 1), backward 50 (the
+    # forward's 13 to alpha, the transmittance division 2, weight 1, the
+    # upstream dot product 8, dL/dalpha 2, its running sum 3, colour/depth
+    # partials 8, the five moments of dL/dpower 11, dL/dopacity 2).
+    # Evaluations are counted as the sum over pixels of the last contributor's
+    # list position, an upper bound (it includes list entries the 8x8-block
+    # culling skips), so the achieved rate is an upper bound too.
+    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 50.0 * n_contrib_sum}
 
 
 def run_ours(args):
@@ -276,6 +279,9 @@ def run_ours(args):
     h2d = sum(g.numel() * 4 for g in gts_h) + sum(x.numel() * 4 for x in lis_h)
     d2h = V * 4 * 8
 
+    map_ops = None if args.skip_map else time_map_ops(P, S, lv, params, grads, cams[0], stream, peaks()[0],
+                                                       peaks()[2])
+
     n_vis, M, nc_sum, P_px = stats
     # instances the compositing kernels gather: bounded by M; use M (upper bound)
     # pyramid: each level-down reads rgb + depth (16 B) and writes a quarter of it
@@ -328,6 +334,7 @@ def run_ours(args):
         "phases_ms": {k: round(v, 4) for k, v in phase_ms.items()},
         "counts": {"visible_pairs": n_vis, "instances": M, "contrib_sum": nc_sum, "pixels": P_px},
         "clocks": clocks,
+        "map_ops": map_ops,
     }
     if rank == 0 and not args.skip_cpu:
         out["cpu_baseline"] = cpu_baseline(wl, pix)
@@ -336,6 +343,65 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def time_map_ops(P, S, lv, params, grads, cam, stream, hbm_peak, peak_kind):
+    """Map maintenance on the bench's map: the Adam step over every parameter
+    (HBM-bound: read parameter, gradient and both moments, write parameter and
+    moments, 28 B per float), expansion by one 50,000-point sweep (with and
+    without the V_p filter of the first keyframe), and opacity pruning."""
+    import torch
+
+    N = params["means"].shape[0]
+    K = params["sh"].shape[1]
+    gm = P.GaussianMap.from_params(params, capacity=N + 120_000)
+    g = gm.grads()
+    for k in P.PARAM_NAMES:
+        g[k].copy_(grads[k])
+    for _ in range(3):
+        gm.adam_step(zero_grads=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ka = 20
+    e0.record(stream)
+    for _ in range(ka):
+        gm.adam_step(zero_grads=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_adam = e0.elapsed_time(e1) / ka
+    adam_bytes = N * (11 + 3 * K) * 28
+    pts, col = S.fresh_scan(50_000, step=0)
+    pts, col = torch.from_numpy(pts).cuda(), torch.from_numpy(col).cuda()
+    n0 = gm.n
+
+    def timed_append(alpha=None, cam=None):
+        ts = []
+        for _ in range(4):
+            gm.n = n0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            added = gm.append(lv, pts, col, cam, 0, alpha)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts[1:])), added
+
+    ms_app, added = timed_append()
+    gm.n = n0
+    _, _, alpha, slot = lv.render(gm.params(), cam, 0)
+    lv.release(slot)
+    ms_app_f, added_f = timed_append(alpha, cam)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    removed = gm.prune(lv, 0.005)
+    torch.cuda.synchronize()
+    ms_prune = (time.perf_counter() - t0) * 1e3
+    return {"adam": {"ms": round(ms_adam, 4), "bytes": adam_bytes,
+                     "achieved_gbs": round(adam_bytes / ms_adam / 1e6, 1),
+                     "frac": round(adam_bytes / ms_adam / 1e6 / hbm_peak, 3), "peak": hbm_peak,
+                     "peak_source": peak_kind, "floats": N * (11 + 3 * K)},
+            "append_50k_sweep_ms": round(ms_app, 3), "appended": added,
+            "append_50k_filtered_ms": None if ms_app_f is None else round(ms_app_f, 3), "appended_filtered": added_f,
+            "prune_ms": round(ms_prune, 3), "pruned": removed, "gaussians": N}
 
 
 def cpu_baseline(wl, pix_total, budget_s=25.0):

@@ -6,5 +6,6 @@ from ._lib import LvigsError, load, library_path  # noqa: F401
 from .context import Context, PARAM_NAMES, loss_noalloc  # noqa: F401
 from .autograd import RenderFunction, render  # noqa: F401
 from .gaussian_map import GaussianMap  # noqa: F401
+from .driver import Keyframe, Mapper, MappingSchedule  # noqa: F401
 
-__all__ = ["Context", "GaussianMap", "loss_noalloc", "RenderFunction", "render", "LvigsError", "load", "library_path", "PARAM_NAMES"]
+__all__ = ["Context", "GaussianMap", "Keyframe", "Mapper", "MappingSchedule", "loss_noalloc", "RenderFunction", "render", "LvigsError", "load", "library_path", "PARAM_NAMES"]

@@ -299,3 +299,40 @@ def test_appended_map_renders_like_oracle(pkg, ctx):
     ok = ref["margin"] > 1e-4
     assert ok.mean() > 0.95
     assert np.abs(rgb.cpu().numpy() - ref["rgb"])[:, ok].max() <= 1e-4
+
+
+def test_mapper_reduces_loss(pkg, ctx):
+    """A short mapping run (expansion from fresh sweeps, coarse-to-fine
+    schedule, Adam) lowers every keyframe's full-resolution loss."""
+    cams = S.trajectory_cameras(3, phase=0.7, W=256, H=192, f=172.0)
+    tg = [S.target_images(c, 300 + i) for i, c in enumerate(cams)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gm = pkg.GaussianMap(capacity=1000, sh_stride_k=16)
+    mapper = pkg.Mapper(ctx, gm, pkg.MappingSchedule(max_iters=30, top_level=2, sh_interval=15, views_per_step=2,
+                                                     seed=1), delay=0)
+    kfs = []
+    for i, c in enumerate(cams):
+        pts, col = S.fresh_scan(20_000, step=10 + i)
+        kf = pkg.Keyframe(cam=c, gt_rgb=t(tg[i][0]), lidar=t(tg[i][1]), points=t(pts), colours=t(col))
+        mapper.add_keyframe(kf)
+        kfs.append(kf)
+    assert gm.n > 20_000  # the first sweep unfiltered, the later ones filtered
+
+    def full_res_losses():
+        out = []
+        for kf in kfs:
+            rgb, depth, alpha, slot = ctx.render(gm.params(), kf.cam, 0)
+            ctx.release(slot)
+            terms, _, _ = ctx.loss(rgb, depth, kf.gt_rgb, kf.lidar, 0.2, 0.1, grads=False)
+            out.append(float(terms[0]))
+        return out
+
+    before = full_res_losses()
+    steps = 0
+    while mapper.step() is not None:
+        steps += 1
+    after = full_res_losses()
+    print(f"  {steps} steps, n={gm.n}, loss before {before} after {after}")
+    assert sum(kf.iters for kf in kfs) == 3 * 30 and steps >= 3 + 87 // 2
+    assert all(a < 0.9 * b for a, b in zip(after, before))
+    assert gm.sh_degree == 3
