@@ -9,8 +9,9 @@
 // per operation in a fixed order (the __f*_rn intrinsics are never
 // contracted), so the keys are reproducible bit for bit on any IEEE machine.
 //
-// Backward, one thread per Gaussian, accumulating over views in registers, so
-// the parameter gradients need no atomics.
+// Backward, one warp per 32 Gaussians: the visible (view, Gaussian) pairs are
+// dealt out over the lanes and summed per Gaussian in shared memory, so the
+// parameter gradients need no global atomics.
 #include "lvigs_internal.cuh"
 
 namespace lvigs {
@@ -309,66 +310,163 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
 
 // ---------------------------------------------------------------------------
 // Backward (a7): chain rule from the screen-space gradients of every view.
+//
+// A warp owns 32 consecutive Gaussians.  Their visible (view, Gaussian) pairs
+// (on average a third of the views) are enumerated warp-wide and dealt out to
+// all 32 lanes, so the per-view chain rule runs with full lanes instead of one
+// lane per Gaussian idling through the views it does not see.  The worker lane
+// takes the owner's mean and Sigma by shuffle and its SH row from shared
+// memory (staged with coalesced loads), and adds its terms to the owner's
+// accumulators in shared memory.  The owner then finishes the per-Gaussian
+// part (Sigma -> scale, rotation; opacity) and the warp writes the SH
+// gradient rows back coalesced.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 4)
+constexpr int kBwdThreads = 128;
+constexpr int kAccScalars = 10; // d_mean 3, dSigma 6 (00,01,02,11,12,22), d_opacity 1
+constexpr int kShRow = 48;      // 16 coefficients x 3 channels
+constexpr int kShPitch = 49;    // staged row pitch: odd, so lanes reading 32 rows hit 32 banks
+constexpr size_t kBwdSmem = sizeof(float) * ((kAccScalars + kShRow) * (kBwdThreads + 1) + kBwdThreads * kShPitch) +
+                            sizeof(uint32_t) * (kBwdThreads / 32) * kMaxViews +
+                            sizeof(int) * (kBwdThreads / 32) * (kMaxViews + 1);
+
+__global__ void __launch_bounds__(kBwdThreads, 4)
 preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ tiles,
                       const GGrad *__restrict__ g2d, ParamGrads G) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.n) return;
-    const size_t N = (size_t)P.n;
+    // accumulators [quantity][owner thread] (+1 column: conflict-free transposed
+    // reads), the warps' SH rows, per-view visibility masks and their prefix counts
+    extern __shared__ float4 smem_bwd[];
+    auto s_sh = reinterpret_cast<float(*)[32 * kShPitch]>(smem_bwd);
+    auto s_acc = reinterpret_cast<float(*)[kBwdThreads + 1]>(&s_sh[kBwdThreads / 32][0]);
+    auto s_mask = reinterpret_cast<uint32_t(*)[kMaxViews]>(&s_acc[kAccScalars + kShRow][0]);
+    auto s_pref = reinterpret_cast<int(*)[kMaxViews + 1]>(&s_mask[kBwdThreads / 32][0]);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, wbase = tid & ~31;
+    const int64_t N = P.n;
+    const int64_t g0 = (int64_t)blockIdx.x * kBwdThreads + wbase; // first Gaussian of the warp
+    const int64_t g = g0 + lane;
+    const bool valid = g < N;
     const int deg = P.sh_degree;
     const int nk = (deg + 1) * (deg + 1);
     const int K = P.sh_stride_k;
-    const float *shg = P.sh + (size_t)g * K * 3;
+    const int row = K * 3;
+    const bool staged = row <= kShRow;
+    const int nrows = (int)(N - g0 < 32 ? N - g0 : 32);
 
-    float d_mean[3] = {0.f, 0.f, 0.f};
-    float dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; // symmetric dL/dSigma (00,01,02,11,12,22)
-    float d_op = 0.f;
-    // SH gradient accumulators live in shared memory ([coefficient][thread],
-    // conflict-free), which keeps the thread's register count and so the
-    // occupancy of this latency-bound loop in check
-    __shared__ float s_dsh[48][128];
-    float(*d_sh)[128] = s_dsh;
-    const int tid = threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < 48; ++k) s_dsh[k][tid] = 0.f;
-    bool any = false;
+    for (int k = 0; k < kAccScalars + kShRow; ++k) s_acc[k][tid] = 0.f;
+    if (staged) {
+        // the warp's rows are one contiguous run: float4 loads, all issued before the stores
+        const float *src = P.sh + g0 * row;
+        const int n = nrows * row;
+        // (rows land at an odd pitch in shared memory)
+        if ((((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
+            constexpr int kMaxIt = 32 * kShRow / 4 / 32;
+            float4 v[kMaxIt];
+#pragma unroll
+            for (int i = 0; i < kMaxIt; ++i) {
+                const int e4 = lane + 32 * i;
+                if (4 * e4 < n) v[i] = __ldg(reinterpret_cast<const float4 *>(src) + e4);
+            }
+#pragma unroll
+            for (int i = 0; i < kMaxIt; ++i) {
+                const int e = 4 * (lane + 32 * i);
+                if (e < n) {
+                    const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int rr = (e + c) / row, cc = (e + c) - rr * row;
+                        s_sh[w][rr * kShPitch + cc] = f[c];
+                    }
+                }
+            }
+        } else {
+            for (int e = lane; e < n; e += 32) {
+                const int rr = e / row, cc = e - rr * row;
+                s_sh[w][rr * kShPitch + cc] = __ldg(src + e);
+            }
+        }
+    }
 
-    const float mx = P.means[3 * (size_t)g], my = P.means[3 * (size_t)g + 1],
-                mz = P.means[3 * (size_t)g + 2];
-    const float *ls = P.log_scales + 3 * (size_t)g;
-    const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
-    const float *q = P.quats + 4 * (size_t)g;
-    const float qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const float qi = 1.f / qnorm;
-    const float qw = q[0] * qi, qx = q[1] * qi, qy = q[2] * qi, qz = q[3] * qi;
-    float r[9];
-    r[0] = 1.f - 2.f * (qy * qy + qz * qz);
-    r[1] = 2.f * (qx * qy - qw * qz);
-    r[2] = 2.f * (qx * qz + qw * qy);
-    r[3] = 2.f * (qx * qy + qw * qz);
-    r[4] = 1.f - 2.f * (qx * qx + qz * qz);
-    r[5] = 2.f * (qy * qz - qw * qx);
-    r[6] = 2.f * (qx * qz - qw * qy);
-    r[7] = 2.f * (qy * qz + qw * qx);
-    r[8] = 1.f - 2.f * (qx * qx + qy * qy);
-    float M[9];
+    // per-Gaussian forward quantities
+    float mx = 0.f, my = 0.f, mz = 0.f, s[3] = {1.f, 1.f, 1.f}, r[9], M[9], Sg6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, qi = 1.f;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 9; ++i) r[i] = M[i] = 0.f;
+    if (valid) {
+        mx = P.means[3 * g];
+        my = P.means[3 * g + 1];
+        mz = P.means[3 * g + 2];
+        const float *ls = P.log_scales + 3 * g;
+        s[0] = expf(ls[0]);
+        s[1] = expf(ls[1]);
+        s[2] = expf(ls[2]);
+        const float *q = P.quats + 4 * g;
+        const float qnorm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        qi = 1.f / qnorm;
+        qw = q[0] * qi;
+        qx = q[1] * qi;
+        qy = q[2] * qi;
+        qz = q[3] * qi;
+        r[0] = 1.f - 2.f * (qy * qy + qz * qz);
+        r[1] = 2.f * (qx * qy - qw * qz);
+        r[2] = 2.f * (qx * qz + qw * qy);
+        r[3] = 2.f * (qx * qy + qw * qz);
+        r[4] = 1.f - 2.f * (qx * qx + qz * qz);
+        r[5] = 2.f * (qy * qz - qw * qx);
+        r[6] = 2.f * (qx * qz - qw * qy);
+        r[7] = 2.f * (qy * qz + qw * qx);
+        r[8] = 1.f - 2.f * (qx * qx + qy * qy);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) M[3 * i + j] = r[3 * i + j] * s[j];
-    float Sg[3][3];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[3 * i + j] = r[3 * i + j] * s[j];
+        int t = 0;
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            Sg[i][j] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j)
+                Sg6[t++] = M[3 * i] * M[3 * j] + M[3 * i + 1] * M[3 * j + 1] + M[3 * i + 2] * M[3 * j + 2];
+    }
 
+    // visible pairs of the warp: one ballot per view, prefix counts
     const int n_views = vsp->n_views;
-#pragma unroll 1
-    for (int vi = 0; vi < n_views; ++vi) {
-        const size_t o = (size_t)vi * N + g;
-        if (tiles[o] == 0) continue;
+    for (int v0 = 0; v0 < n_views; v0 += 8) {
+        uint32_t t8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t8[j] = (valid && v0 + j < n_views) ? tiles[(size_t)(v0 + j) * N + g] : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t m = __ballot_sync(0xffffffffu, t8[j] != 0);
+            if (lane == 0 && v0 + j < n_views) s_mask[w][v0 + j] = m;
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int acc = 0;
+        for (int vi = 0; vi < n_views; ++vi) {
+            s_pref[w][vi] = acc;
+            acc += __popc(s_mask[w][vi]);
+        }
+        s_pref[w][n_views] = acc;
+    }
+    __syncthreads(); // accumulators, staged rows and masks are visible to every lane
+    const int total = s_pref[w][n_views];
+
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        const bool has = p < total;
+        int vi = 0, src = lane;
+        if (has) {
+            while (vi + 1 < n_views && s_pref[w][vi + 1] <= p) ++vi;
+            src = (int)__fns(s_mask[w][vi], 0, p - s_pref[w][vi] + 1);
+        }
+        const float gx = __shfl_sync(0xffffffffu, mx, src);
+        const float gy = __shfl_sync(0xffffffffu, my, src);
+        const float gz = __shfl_sync(0xffffffffu, mz, src);
+        float S6[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) S6[t] = __shfl_sync(0xffffffffu, Sg6[t], src);
+        if (!has) continue;
+        const size_t o = (size_t)vi * N + (size_t)(g0 + src);
         const GGrad gg = g2d[o];
         const float mx_ = gg.g0.x, my_ = gg.g0.y, mxx = gg.g0.z, mxy = gg.g0.w;
         const float myy = gg.g1.x, dop = gg.g1.y, ddepth = gg.g1.z;
@@ -376,11 +474,11 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         if (mx_ == 0.f && my_ == 0.f && mxx == 0.f && mxy == 0.f && myy == 0.f && dop == 0.f &&
             ddepth == 0.f && drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f)
             continue;
-        any = true;
+        const float Sg[3][3] = {{S6[0], S6[1], S6[2]}, {S6[1], S6[3], S6[4]}, {S6[2], S6[4], S6[5]}};
         const ViewDesc &V = vsp->v[vi];
-        const float px = V.R[0] * mx + V.R[1] * my + V.R[2] * mz + V.t[0];
-        const float py = V.R[3] * mx + V.R[4] * my + V.R[5] * mz + V.t[1];
-        const float pz = V.R[6] * mx + V.R[7] * my + V.R[8] * mz + V.t[2];
+        const float px = V.R[0] * gx + V.R[1] * gy + V.R[2] * gz + V.t[0];
+        const float py = V.R[3] * gx + V.R[4] * gy + V.R[5] * gz + V.t[1];
+        const float pz = V.R[6] * gx + V.R[7] * gy + V.R[8] * gz + V.t[2];
         const float iz = 1.f / pz;
         const float xz = px * iz, yz = py * iz;
         const bool clx = xz < -V.limx || xz > V.limx;
@@ -415,6 +513,8 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         const float da = -c * c * id2 * dA + b * c * id2 * dB + (id - a * c * id2) * dC;
         const float dc = (id - a * c * id2) * dA + a * b * id2 * dB - a * a * id2 * dC;
         const float db = 2.f * b * c * id2 * dA + (-id - 2.f * b * b * id2) * dB + 2.f * a * b * id2 * dC;
+        float *acc_col = &s_acc[0][wbase + src];
+        constexpr int ld = kBwdThreads + 1;
         // a = T0 Sigma T0^T, b = T0 Sigma T1^T, c = T1 Sigma T1^T
 #pragma unroll
         for (int rr = 0; rr < 3; ++rr)
@@ -424,7 +524,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
                           0.5f * db * (T[0][rr] * T[1][ss] + T[1][rr] * T[0][ss]);
                 // off-diagonal entries collect both symmetric positions
                 if (ss != rr) v *= 2.f;
-                dSig[rr == 0 ? ss : (rr == 1 ? 2 + ss : 5)] += v;
+                atomicAdd(acc_col + ld * (3 + (rr == 0 ? ss : (rr == 1 ? 2 + ss : 5))), v);
             }
         float dT[2][3];
 #pragma unroll
@@ -459,12 +559,11 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         dpx += du * V.fx * iz;
         dpy += dv * V.fy * iz;
         dpz += -(du * V.fx * px + dv * V.fy * py) * iz2 + ddepth;
+        float dm[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) d_mean[k] += V.R[k] * dpx + V.R[3 + k] * dpy + V.R[6 + k] * dpz;
-        // opacity
-        d_op += dop;
+        for (int k = 0; k < 3; ++k) dm[k] = V.R[k] * dpx + V.R[3 + k] * dpy + V.R[6 + k] * dpz;
         // colour through the SH basis at the view direction
-        float ex = mx - V.campos[0], ey = my - V.campos[1], ez = mz - V.campos[2];
+        float ex = gx - V.campos[0], ey = gy - V.campos[1], ez = gz - V.campos[2];
         const float len = sqrtf(ex * ex + ey * ey + ez * ez);
         const float il = 1.f / len;
         ex *= il;
@@ -472,100 +571,105 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         ez *= il;
         float Y[16];
         sh_values(deg, ex, ey, ez, Y);
-        float w[16];
+        const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
+        float w16[16];
         float m3[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float raw = 0.5f;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                if (k < nk) raw += Y[k] * __ldg(shg + 3 * k + ch);
+                if (k < nk) raw += Y[k] * shg[3 * k + ch];
             m3[ch] = raw < 0.f ? 0.f : drgb[ch];
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            w[k] = 0.f;
+            w16[k] = 0.f;
             if (k < nk) {
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    d_sh[3 * k + ch][tid] += Y[k] * m3[ch];
-                    w[k] += m3[ch] * __ldg(shg + 3 * k + ch);
+                    atomicAdd(acc_col + ld * (kAccScalars + 3 * k + ch), Y[k] * m3[ch]);
+                    w16[k] += m3[ch] * shg[3 * k + ch];
                 }
             }
         }
-        const float3 gd = sh_weighted_grad(deg, ex, ey, ez, w);
+        const float3 gd = sh_weighted_grad(deg, ex, ey, ez, w16);
         const float dd = gd.x * ex + gd.y * ey + gd.z * ez;
-        d_mean[0] += (gd.x - ex * dd) * il;
-        d_mean[1] += (gd.y - ey * dd) * il;
-        d_mean[2] += (gd.z - ez * dd) * il;
+        dm[0] += (gd.x - ex * dd) * il;
+        dm[1] += (gd.y - ey * dd) * il;
+        dm[2] += (gd.z - ez * dd) * il;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(acc_col + ld * k, dm[k]);
+        atomicAdd(acc_col + ld * 9, dop);
     }
+    __syncwarp();
 
-    // Sigma = M M^T with M = R diag(s): dM = 2 dSigma_sym M
-    float dS[3][3];
-    dS[0][0] = dSig[0];
-    dS[1][1] = dSig[3];
-    dS[2][2] = dSig[5];
-    dS[0][1] = dS[1][0] = 0.5f * dSig[1];
-    dS[0][2] = dS[2][0] = 0.5f * dSig[2];
-    dS[1][2] = dS[2][1] = 0.5f * dSig[4];
-    float d_ls[3], dR[9];
+    if (valid) {
+        const float dSig[6] = {s_acc[3][tid], s_acc[4][tid], s_acc[5][tid], s_acc[6][tid], s_acc[7][tid],
+                               s_acc[8][tid]};
+        const float d_mean[3] = {s_acc[0][tid], s_acc[1][tid], s_acc[2][tid]};
+        const float d_op = s_acc[9][tid];
+        // Sigma = M M^T with M = R diag(s): dM = 2 dSigma_sym M
+        float dS[3][3];
+        dS[0][0] = dSig[0];
+        dS[1][1] = dSig[3];
+        dS[2][2] = dSig[5];
+        dS[0][1] = dS[1][0] = 0.5f * dSig[1];
+        dS[0][2] = dS[2][0] = 0.5f * dSig[2];
+        dS[1][2] = dS[2][1] = 0.5f * dSig[4];
+        float d_ls[3], dR[9];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        float dsj = 0.f;
+        for (int j = 0; j < 3; ++j) {
+            float dsj = 0.f;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float dMij = 2.f * (dS[i][0] * M[j] + dS[i][1] * M[3 + j] + dS[i][2] * M[6 + j]);
-            dsj += dMij * r[3 * i + j];
-            dR[3 * i + j] = dMij * s[j];
+            for (int i = 0; i < 3; ++i) {
+                const float dMij = 2.f * (dS[i][0] * M[j] + dS[i][1] * M[3 + j] + dS[i][2] * M[6 + j]);
+                dsj += dMij * r[3 * i + j];
+                dR[3 * i + j] = dMij * s[j];
+            }
+            d_ls[j] = dsj * s[j];
         }
-        d_ls[j] = dsj * s[j];
+        float dq[4];
+        dq[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
+        dq[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
+                       qw * dR[7] - 2.f * qx * dR[8]);
+        dq[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
+                       qz * dR[7] - 2.f * qy * dR[8]);
+        dq[3] = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
+                       qy * dR[5] + qx * dR[6] + qy * dR[7]);
+        const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
+        const float qn[4] = {qw, qx, qy, qz};
+        const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
+        const float d_logit = d_op * o * (1.f - o);
+        if (!G.accumulate) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                G.d_means[3 * g + k] = d_mean[k];
+                G.d_log_scales[3 * g + k] = d_ls[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] = (dq[k] - qn[k] * qdot) * qi;
+            G.d_opacity_logits[g] = d_logit;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                G.d_means[3 * g + k] += d_mean[k];
+                G.d_log_scales[3 * g + k] += d_ls[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] += (dq[k] - qn[k] * qdot) * qi;
+            G.d_opacity_logits[g] += d_logit;
+        }
     }
-    float dq[4];
-    dq[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
-    dq[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
-                   qw * dR[7] - 2.f * qx * dR[8]);
-    dq[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
-                   qz * dR[7] - 2.f * qy * dR[8]);
-    dq[3] = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
-                   qy * dR[5] + qx * dR[6] + qy * dR[7]);
-    const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
-    const float qn[4] = {qw, qx, qy, qz};
-    const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
-    const float d_logit = d_op * o * (1.f - o);
-
-    if (!G.accumulate) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            G.d_means[3 * (size_t)g + k] = d_mean[k];
-            G.d_log_scales[3 * (size_t)g + k] = d_ls[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) G.d_quats[4 * (size_t)g + k] = (dq[k] - qn[k] * qdot) * qi;
-        G.d_opacity_logits[g] = d_logit;
-        float *dsh = G.d_sh + (size_t)g * K * 3;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = d_sh[3 * k + ch][tid];
-        for (int k = 16; k < K; ++k)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] = 0.f;
-    } else if (any) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            G.d_means[3 * (size_t)g + k] += d_mean[k];
-            G.d_log_scales[3 * (size_t)g + k] += d_ls[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) G.d_quats[4 * (size_t)g + k] += (dq[k] - qn[k] * qdot) * qi;
-        G.d_opacity_logits[g] += d_logit;
-        float *dsh = G.d_sh + (size_t)g * K * 3;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < nk)
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) dsh[3 * k + ch] += d_sh[3 * k + ch][tid];
+    // SH gradient rows of the warp's Gaussians, contiguous in memory: written
+    // with consecutive lanes on consecutive floats
+    float *dst = G.d_sh + g0 * row;
+    for (int e = lane; e < nrows * row; e += 32) {
+        const int rw = e / row, col = e - rw * row;
+        const bool live = col < 3 * nk && col < kShRow;
+        const float v = live ? s_acc[kAccScalars + col][wbase + rw] : 0.f;
+        if (!G.accumulate) dst[e] = v;
+        else if (live) dst[e] += v;
     }
 }
 
@@ -582,9 +686,16 @@ void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs, GRec *recs, 
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs, const uint32_t *tiles,
                            const GGrad *g2d, const ParamGrads &G, cudaStream_t s) {
     if (P.n <= 0) return;
-    const int threads = 128;
-    const int blocks = (P.n + threads - 1) / threads;
-    preprocess_bwd_kernel<<<blocks, threads, 0, s>>>(P, vs, tiles, g2d, G);
+    // the dynamic shared-memory limit is raised once per device
+    static uint64_t attr_set = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !((attr_set >> dev) & 1u)) {
+        cudaFuncSetAttribute(preprocess_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+        attr_set |= (uint64_t)1 << dev;
+    }
+    const int blocks = (P.n + kBwdThreads - 1) / kBwdThreads;
+    preprocess_bwd_kernel<<<blocks, kBwdThreads, kBwdSmem, s>>>(P, vs, tiles, g2d, G);
 }
 
 } // namespace lvigs
