@@ -421,6 +421,20 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     return LVIGS_OK;
 }
 
+// The backward's work order: the plan's pairs sorted by decreasing expected
+// walk (written over the forward's order, which the forward no longer needs).
+ChunkPlan backward_plan(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
+    ChunkPlan cp = st.plan();
+    uint32_t *cnt = (uint32_t *)st.counters.p;
+    launch_bwd_pair_keys(st.vs, (const ViewSet *)st.vs_dev.p, cp, (const int32_t *)st.n_contrib.p,
+                         (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
+    const int alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, (uint32_t *)st.pair_k2.p,
+                                      (uint32_t *)st.pair_v2.p, cnt + 4, st.pair_cap, 11,
+                                      (uint32_t *)ctx->radix_tmp.p, s);
+    cp.pair_order = (const uint32_t *)(alt ? st.pair_v2.p : st.pair_v.p);
+    return cp;
+}
+
 lvigs_status upload_viewset(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
     LV_TRY(ensure(ctx, st.vs_dev, sizeof(ViewSet)));
     // the pinned staging copy is reused once the previous upload has landed
@@ -613,9 +627,10 @@ lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
     vg.d_alpha[0] = dL_dalpha;
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
+        const ChunkPlan bp = backward_plan(ctx, *st, s);
         launch_composite_bwd(st->vs, (const ViewSet *)st->vs_dev.p, (const uint2 *)st->ranges.p, st->sorted_vals(),
                              (const GRec *)st->recs.p, vg, (const float *)st->final_T.p,
-                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, st->plan(),
+                             (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, bp,
                              (uint32_t *)st->counters.p + 3, s, ctx->bm);
     }
     ParamGrads G{grads->d_means, grads->d_log_scales, grads->d_quats, grads->d_opacity_logits, grads->d_sh,
@@ -884,9 +899,10 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     if (VN > 0) LV_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, (size_t)VN * sizeof(GGrad), s));
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
+        const ChunkPlan bp = backward_plan(ctx, st, s);
         launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
-                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p,
-                             st.plan(), (uint32_t *)st.counters.p + 3, s, ctx->bm);
+                             (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, bp,
+                             (uint32_t *)st.counters.p + 3, s, ctx->bm);
     }
     ParamGrads G{gr->d_means, gr->d_log_scales, gr->d_quats, gr->d_opacity_logits, gr->d_sh, gr->accumulate};
     {

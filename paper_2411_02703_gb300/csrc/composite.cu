@@ -691,6 +691,42 @@ __global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const u
     }
 }
 
+// Backward work order: (tile, chunk) pairs by decreasing expected walk, the
+// part of the chunk before the tile's furthest last contributor; the longest
+// items start first, which keeps the tail of the persistent kernel short.
+// One warp per pair; key = L - walk (0 first), L + 1 for pairs of no tile.
+template <int TW, int TH>
+__global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp,
+                                     const int32_t *__restrict__ n_contrib, uint32_t *__restrict__ keys,
+                                     uint32_t *__restrict__ vals) {
+    using Gm = Geometry<TW, TH>;
+    const uint32_t n = min(*cp.n_pairs, cp.pair_cap);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
+        const uint32_t t = cp.pair_tile[p];
+        uint32_t key = (uint32_t)cp.L + 1u;
+        if (t < vsp->total_tiles) {
+            const uint32_t k = p - cp.chunk_base[t];
+            const ViewDesc &V = vsp->v[view_of_tile(*vsp, t)];
+            const uint32_t lt = t - V.tile_base;
+            const int tx = (int)(lt % (uint32_t)V.tiles_x), ty = (int)(lt / (uint32_t)V.tiles_x);
+            int mx = 0;
+            for (int i = lane; i < Gm::TPX; i += 32) {
+                const int px = tx * TW + i % TW, py = ty * TH + i / TW;
+                if (px < V.W && py < V.H) mx = max(mx, n_contrib[V.pix_base + (size_t)py * V.W + px]);
+            }
+            mx = __reduce_max_sync(0xffffffffu, mx);
+            const int64_t walk = (int64_t)mx - (int64_t)k * cp.L;
+            key = (uint32_t)cp.L - (uint32_t)(walk < 0 ? 0 : (walk > cp.L ? cp.L : walk));
+        }
+        if (lane == 0) {
+            keys[p] = key;
+            vals[p] = p;
+        }
+    }
+}
+
 template <typename K>
 unsigned persistent_grid(K kernel, uint64_t max_items) {
     int dev = 0, sms = 152, per_sm = 1;
@@ -788,6 +824,19 @@ void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uin
     int blocks = (int)((cp.pair_cap + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
     pair_keys_kernel<<<blocks, 256, 0, s>>>(cp.pair_tile, cp.chunk_base, cp.n_pairs, cp.pair_cap, n_tiles, keys, vals);
+}
+
+void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan &cp, const int32_t *n_contrib,
+                          uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+    if (cp.pair_cap == 0) return;
+    uint64_t blocks = ((uint64_t)cp.pair_cap * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (vs.tile_w == 16 && vs.tile_h == 16)
+        bwd_pair_keys_kernel<16, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
+    else if (vs.tile_w == 8 && vs.tile_h == 8)
+        bwd_pair_keys_kernel<8, 8><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
+    else if (vs.tile_w == 32 && vs.tile_h == 16)
+        bwd_pair_keys_kernel<32, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
 }
 
 size_t chunk_slot_bytes(int tile_w, int tile_h) { return (size_t)kFields * tile_w * tile_h * sizeof(float); }

@@ -160,6 +160,9 @@ void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t 
 void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s);
 void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s);
 size_t chunk_slot_bytes(int tile_w, int tile_h);
+// Keys of the backward work order (11 bits: L - expected walk of each pair).
+void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan &cp, const int32_t *n_contrib,
+                          uint32_t *keys, uint32_t *vals, cudaStream_t s);
 
 // Compositing: persistent warps, one (tile, chunk, 8x8 block) per work item;
 // each stages 32 * bm Gaussians per round (bm = 1 or 2).  `queue` is one device
