@@ -55,7 +55,8 @@ constexpr float kTMin = 1e-4f;
 constexpr int PB = 8;  // warp pixel block is PB x PB
 constexpr int PPT = 2; // pixels per lane (rows 2r, 2r+1 of the block)
 constexpr int kWarpsPerCta = 4;
-constexpr int kFields = 6; // per (pixel, chunk) slot
+constexpr int kFields = 6; // per (pixel, chunk) slot and checkpoint
+constexpr int kSub = 8;    // checkpoint groups per chunk: after each eighth (the last is the chunk's end)
 
 // does the alpha box of record (a, b, c) meet the block [x0, x0+7] x [y0, y0+7]?
 __device__ __forceinline__ bool meets(const float4 a, const float4 b, const float4 c, float x0, float y0) {
@@ -129,27 +130,59 @@ __device__ __forceinline__ int gather_cull(const uint32_t *__restrict__ inst_val
     return n;
 }
 
+// Where a walk stores its checkpoints: the (pixel, chunk) slot's groups.
+struct Checkpoints {
+    float *g0;    // group 0, field 0 of the slot (null: no checkpoints)
+    int every;    // list entries between checkpoints
+    int tpx, lp0, tw;
+};
+
 // Front-to-back walk of list entries [lo, hi) for the lane's pixels, from the
 // state passed in.  Pixels with done[k] set are left alone; stopped[k] is set
-// when the pixel stops (the transmittance test) inside this walk.
-template <int BM>
+// when the pixel stops (the transmittance test) inside this walk.  With
+// CKPT the state after every `every` entries (except at hi) is stored; with
+// START a pixel takes no entry before list position start[k].
+template <int BM, bool CKPT, bool START>
 __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs,
                                          uint32_t rg_x, uint32_t lo, uint32_t hi, float fpx, int py0, float fx0,
                                          float fy0, const Smem &sm, int lane, float T[PPT], float C0[PPT],
                                          float C1[PPT], float C2[PPT], float D[PPT], int last[PPT], bool done[PPT],
-                                         bool stopped[PPT]) {
+                                         bool stopped[PPT], const Checkpoints &ck, const int start[PPT]) {
     constexpr int B = 32 * BM;
     bool tdone = done[0] && done[1];
+    // checkpoints lie at lo + (m + 1) * every < hi; next_ck is the next to store
+    const int n_ck = (CKPT && ck.g0 && hi > lo) ? min(kSub - 1, (int)((hi - lo - 1) / (uint32_t)ck.every)) : 0;
+    int next_ck = 0;
+    auto store_ck = [&](int m) {
+        float *g = ck.g0 + (size_t)m * kFields * ck.tpx;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            const int lp = ck.lp0 + k * ck.tw;
+            g[0 * ck.tpx + lp] = C0[k];
+            g[1 * ck.tpx + lp] = C1[k];
+            g[2 * ck.tpx + lp] = C2[k];
+            g[3 * ck.tpx + lp] = D[k];
+            g[4 * ck.tpx + lp] = T[k];
+            g[5 * ck.tpx + lp] = __int_as_float(last[k] | (stopped[k] ? (int)0x80000000 : 0));
+        }
+    };
     for (uint32_t base = lo; base < hi; base += B) {
-        if (__all_sync(0xffffffffu, tdone)) break;
+        if (__all_sync(0xffffffffu, tdone)) {
+            // every pixel is finished: the remaining checkpoints hold the final state
+            for (; next_ck < n_ck; ++next_ck) store_ck(next_ck);
+            break;
+        }
         const int n = gather_cull<BM, false>(inst_vals, recs, rg_x, base, hi, fx0, fy0, sm, lane);
         for (int q = 0; q < n && !tdone; ++q) {
             const float4 a = sm.A[q];
             const float4 b = sm.B[q];
             const float dx = a.x - fpx;
+            int qpos = 0;
+            if (START) qpos = sm.Pos[q];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (done[k]) continue;
+                if (START && qpos < start[k]) continue;
                 const float dy = a.y - (float)(py0 + k);
                 const float power = gauss_power(a.z, a.w, b.x, dx, dy);
                 if (power > 0.f) continue;
@@ -173,6 +206,8 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             tdone = done[0] && done[1];
         }
         __syncwarp();
+        if (CKPT && next_ck < n_ck && base + B - lo == (uint32_t)(next_ck + 1) * (uint32_t)ck.every)
+            store_ck(next_ck++);
     }
 }
 
@@ -192,8 +227,13 @@ __device__ __forceinline__ void write_final(const ViewDesc &V, const ViewImages 
     }
 }
 
+// Field of checkpoint group `sub` of a (pixel, chunk) slot; slot_field is the
+// chunk's end (the last group), the only one the combine and backward state use.
+__device__ __forceinline__ float *slot_group(const ChunkPlan &cp, uint32_t slot, int sub, int field, int tpx) {
+    return cp.part + (((size_t)slot * kSub + sub) * kFields + field) * (size_t)tpx;
+}
 __device__ __forceinline__ float *slot_field(const ChunkPlan &cp, uint32_t slot, int field, int tpx) {
-    return cp.part + ((size_t)slot * kFields + field) * (size_t)tpx;
+    return slot_group(cp, slot, kSub - 1, field, tpx);
 }
 
 __device__ __forceinline__ uint32_t take_item(uint32_t *queue, int lane) {
@@ -202,9 +242,10 @@ __device__ __forceinline__ uint32_t take_item(uint32_t *queue, int lane) {
     return __shfl_sync(0xffffffffu, item, 0);
 }
 
-// Phase 1: (tile, chunk, block) items.
+// Phase 1: (tile, chunk, block) items.  (Six CTAs per SM: the register cap
+// that gives beats the occupancy the unconstrained allocation leaves.)
 template <int TW, int TH, int BM>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
 composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
                      const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
                      float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
@@ -249,8 +290,10 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 if (__ldcg(cp.stop_at + gp) < k) done[j] = true;
             }
         }
-        fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2,
-                     D, last, done, stopped);
+        Checkpoints ck{nullptr, cp.L / kSub, Gm::TPX, bp.lp0, TW};
+        if (nch > 1 && cp.part_base[gt] + k < cp.slot_cap) ck.g0 = slot_group(cp, cp.part_base[gt] + k, 0, 0, Gm::TPX);
+        fwd_walk<BM, true, false>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0,
+                                  C1, C2, D, last, done, stopped, ck, nullptr);
         if (nch > 1) {
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
@@ -279,12 +322,14 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     }
 }
 
-// Per-pixel state between the combine kernels (multi-chunk tiles only):
-// stop chunk (or -1), transmittance before it, colour / depth before it, last.
+// Per-pixel state between the combine kernels (multi-chunk tiles only): stop
+// chunk (or -1) and the eighth of it where the walk resumes; transmittance
+// and colour / depth at the chunk's start; the state at the resume point.
 struct PixState {
-    int stop;
+    int stop, sub;
     float Tin, C0, C1, C2, D;
-    int last;
+    float Tc, Cc0, Cc1, Cc2, Dc;
+    int lastc;
     int pad;
 };
 
@@ -293,8 +338,9 @@ struct PixState {
 // are final here.
 template <int TW, int TH>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-combine_scan_kernel(const ViewSet *__restrict__ vsp, ViewImages out, float *__restrict__ final_T,
-                    int32_t *__restrict__ n_contrib, ChunkPlan cp, PixState *__restrict__ ps, uint32_t total_tiles) {
+combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges, ViewImages out,
+                    float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
+                    PixState *__restrict__ ps, uint32_t total_tiles) {
     using Gm = Geometry<TW, TH>;
     constexpr int TPX = Gm::TPX;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -332,7 +378,32 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, ViewImages out, float *__re
             if (lk) last = lk;
         }
         const size_t gp = V.pix_base + (size_t)py * V.W + bp.px;
-        ps[gp] = PixState{stop, T, C0, C1, C2, D, last, 0};
+        PixState st{stop, 0, T, C0, C1, C2, D, T, C0, C1, C2, D, last, 0};
+        if (stop >= 0) {
+            // the part of the stop chunk that holds the stop: the first checkpoint
+            // whose transmittance is (within 1%) below the limit, or whose local walk
+            // had stopped; the walk resumes from the checkpoint before it
+            const uint2 rg = ranges[gt];
+            const int64_t rest = (int64_t)rg.y - (int64_t)rg.x - (int64_t)stop * cp.L;
+            const int clen = (int)(rest < cp.L ? rest : cp.L);
+            const int every = cp.L / kSub;
+            int m = 0;
+            for (; m < kSub - 1; ++m) {
+                if ((m + 1) * every >= clen) break; // checkpoint m lies past the chunk's end: not written
+                const uint32_t sl = s0 + (uint32_t)stop;
+                const float Tm = slot_group(cp, sl, m, 4, TPX)[lp];
+                const int lm = __float_as_int(slot_group(cp, sl, m, 5, TPX)[lp]);
+                if ((lm & (int)0x80000000) || __fmul_rn(T, Tm) < 1.01f * kTMin) break;
+                st.Tc = __fmul_rn(T, Tm);
+                st.Cc0 = fmaf(T, slot_group(cp, sl, m, 0, TPX)[lp], C0);
+                st.Cc1 = fmaf(T, slot_group(cp, sl, m, 1, TPX)[lp], C1);
+                st.Cc2 = fmaf(T, slot_group(cp, sl, m, 2, TPX)[lp], C2);
+                st.Dc = fmaf(T, slot_group(cp, sl, m, 3, TPX)[lp], D);
+                if (lm) st.lastc = lm;
+            }
+            st.sub = m;
+        }
+        ps[gp] = st;
         if (stop < 0) write_final(V, out, vi, final_T, n_contrib, bp.px, py, T, C0, C1, C2, D, last);
     }
 }
@@ -341,7 +412,7 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, ViewImages out, float *__re
 // (tile, chunk, block) item per warp, for the pixels that stop in that chunk.
 // Writes their final values and the chunk's contribution (backward state).
 template <int TW, int TH, int BM>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
 combine_walk_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
                     const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewImages out,
                     float *__restrict__ final_T, int32_t *__restrict__ n_contrib, ChunkPlan cp,
@@ -369,41 +440,49 @@ combine_walk_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
         const ViewDesc &V = vsp->v[vi];
         const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
         float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT], b0[PPT], b1[PPT], b2[PPT], bd[PPT];
-        int last[PPT];
+        int last[PPT], start[PPT];
         bool done[PPT], stopped[PPT];
         bool any = false;
+        int first = 0x7fffffff; // earliest resume position of the lane's pixels (list-relative)
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             done[j] = true;
             stopped[j] = false;
             T[j] = Tin[j] = 1.f;
             C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+            b0[j] = b1[j] = b2[j] = bd[j] = 0.f;
             last[j] = 0;
+            start[j] = 0;
             const int py = bp.py0 + j;
             if (bp.px < V.W && py < V.H) {
                 const PixState st = ps[V.pix_base + (size_t)py * V.W + bp.px];
                 if (st.stop == (int)k) {
                     done[j] = false;
                     any = true;
-                    T[j] = Tin[j] = st.Tin;
-                    C0[j] = st.C0;
-                    C1[j] = st.C1;
-                    C2[j] = st.C2;
-                    D[j] = st.D;
-                    last[j] = st.last;
+                    Tin[j] = st.Tin;
+                    b0[j] = st.C0;
+                    b1[j] = st.C1;
+                    b2[j] = st.C2;
+                    bd[j] = st.D;
+                    T[j] = st.Tc;
+                    C0[j] = st.Cc0;
+                    C1[j] = st.Cc1;
+                    C2[j] = st.Cc2;
+                    D[j] = st.Dc;
+                    last[j] = st.lastc;
+                    start[j] = (int)(k * (uint32_t)cp.L) + st.sub * (cp.L / kSub);
+                    first = min(first, start[j]);
                 }
             }
-            b0[j] = C0[j];
-            b1[j] = C1[j];
-            b2[j] = C2[j];
-            bd[j] = D[j];
         }
         if (!__any_sync(0xffffffffu, any)) continue;
+        first = __reduce_min_sync(0xffffffffu, first);
         const uint2 rg = ranges[gt];
-        const uint32_t lo = rg.x + k * (uint32_t)cp.L;
-        const uint32_t hi = min(rg.y, lo + (uint32_t)cp.L);
-        fwd_walk<BM>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0, C1, C2, D,
-                     last, done, stopped);
+        const uint32_t lo = rg.x + (uint32_t)first;
+        const uint32_t hi = min(rg.y, rg.x + k * (uint32_t)cp.L + (uint32_t)cp.L);
+        const Checkpoints no_ck{nullptr, 1, Gm::TPX, 0, TW};
+        fwd_walk<BM, false, true>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0,
+                                  C1, C2, D, last, done, stopped, no_ck, start);
         const uint32_t slot = cp.part_base[gt] + k;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -521,7 +600,7 @@ __device__ __forceinline__ float reduce_scatter10(const float v[10], int lane, i
 __device__ __forceinline__ int grad_offset(int idx) { return idx < 6 ? idx : (idx < 9 ? idx + 2 : 6); }
 
 template <int TW, int TH, int BM>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
 composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
                      const uint32_t *__restrict__ inst_vals, const GRec *__restrict__ recs, ViewGrads G,
                      const float *__restrict__ final_T, const int32_t *__restrict__ n_contrib,
@@ -755,8 +834,8 @@ void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, cons
                                                                       n_contrib, cp, queue);
     }
     if (part & 2) {
-        combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, out, final_T, n_contrib, cp, ps,
-                                                                            vs.total_tiles);
+        combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, ranges, out, final_T, n_contrib, cp,
+                                                                            ps, vs.total_tiles);
         cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
         combine_walk_kernel<TW, TH, BM><<<persistent_grid(combine_walk_kernel<TW, TH, BM>, max_items),
                                           kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
@@ -839,7 +918,9 @@ void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan
         bwd_pair_keys_kernel<32, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
 }
 
-size_t chunk_slot_bytes(int tile_w, int tile_h) { return (size_t)kFields * tile_w * tile_h * sizeof(float); }
+size_t chunk_slot_bytes(int tile_w, int tile_h) {
+    return (size_t)kFields * kSub * tile_w * tile_h * sizeof(float);
+}
 
 size_t pix_state_bytes() { return sizeof(PixState); }
 

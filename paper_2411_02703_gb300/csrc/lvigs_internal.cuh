@@ -150,7 +150,7 @@ struct ChunkPlan {
     const uint32_t *part_base;  // [tiles] first slot of a multi-chunk tile
     const uint32_t *pair_tile;  // [pair_cap] tile of each pair
     const uint32_t *n_pairs;    // device count of pairs
-    float *part;                // [slot_cap] slots of 6 x tile_w x tile_h floats
+    float *part;                // [slot_cap] slots: 8 checkpoint groups of 6 x tile_w x tile_h floats
     uint32_t pair_cap, slot_cap;
     const uint32_t *pair_order; // [pair_cap] work order (chunk-major), or null
     uint32_t *stop_at;          // [total pixels] first chunk with a local stop (reset to ~0)
