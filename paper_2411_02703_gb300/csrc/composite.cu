@@ -177,6 +177,7 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             const float4 a = sm.A[q];
             const float4 b = sm.B[q];
             const float dx = a.x - fpx;
+            const float a2dx = __fmul_rn(a.z, dx);
             int qpos = 0;
             if (START) qpos = sm.Pos[q];
 #pragma unroll
@@ -184,9 +185,9 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
                 if (done[k]) continue;
                 if (START && qpos < start[k]) continue;
                 const float dy = a.y - (float)(py0 + k);
-                const float power = gauss_power(a.z, a.w, b.x, dx, dy);
-                if (power > 0.f) continue;
-                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, __expf(power)));
+                const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy);
+                if (e2 > 0.f) continue;
+                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, exp2_approx(e2)));
                 if (alpha < kAlphaMin) continue;
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
@@ -679,6 +680,7 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 const float4 c = sm.C[q];
                 const int pos = sm.Pos[q];
                 const float dx = a.x - fpx;
+                const float a2dx = __fmul_rn(a.z, dx);
                 // v: sums over the lane's pixels of dp dx, dp dy, dp dx^2, dp dx dy,
                 // dp dy^2 (dp = dL/dpower), dL/do, and w g_R, w g_G, w g_B, w g_D;
                 // the conic is applied per Gaussian in the chain rule that follows
@@ -690,9 +692,9 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 for (int j = 0; j < PPT; ++j) {
                     if (pos >= last[j]) continue;
                     const float dy = a.y - (float)(bp.py0 + j);
-                    const float power = gauss_power(a.z, a.w, b.x, dx, dy);
-                    if (power > 0.f) continue;
-                    const float G_ = __expf(power);
+                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy);
+                    if (e2 > 0.f) continue;
+                    const float G_ = exp2_approx(e2);
                     const float oG = __fmul_rn(b.y, G_);
                     const float alpha = fminf(kAlphaMax, oG);
                     if (alpha < kAlphaMin) continue;

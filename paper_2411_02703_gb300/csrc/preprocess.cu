@@ -300,9 +300,12 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
             ex = (a > 0.f) ? sqrtf(2.f * tau * a) + 0.05f : 1e30f;
             ey = (c > 0.f) ? sqrtf(2.f * tau * c) + 0.05f : 1e30f;
         }
+        // conic [[A, B], [B, C]] = [[c, -b], [-b, a]] / det, stored as the
+        // coefficients of the base-2 exponent log2(e) * power (see GRec)
+        constexpr float kLog2e = 1.4426950408889634f;
         GRec rec;
-        rec.a = make_float4(u, v, c * inv_det, -b * inv_det);
-        rec.b = make_float4(a * inv_det, opacity, pz, ex);
+        rec.a = make_float4(u, v, (c * inv_det) * (-0.5f * kLog2e), (b * inv_det) * kLog2e);
+        rec.b = make_float4((a * inv_det) * (-0.5f * kLog2e), opacity, pz, ex);
         rec.c = make_float4(rgb[0], rgb[1], rgb[2], ey);
         recs[o] = rec;
     }
