@@ -802,6 +802,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     // 1. targets at each view's level (Sec. III-D)
     const float *gt_l[kMaxViews];
     const float *li_l[kMaxViews];
+    PyrViews pv[LVIGS_MAX_LEVEL + 1] = {};
     for (int v = 0; v < V; ++v) {
         const lvigs_camera &c = b->cameras[v];
         const size_t P0 = (size_t)c.width * c.height;
@@ -817,21 +818,29 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
                 lsrc = (const float *)ctx->lidar_stage[v].p;
             }
         }
-        int W = c.width, H = c.height;
-        Phase ph(ctx, LVIGS_PHASE_PYRAMID, s);
-        for (int l = 1; l <= b->levels[v]; ++l) {
-            const int W2 = W / 2, H2 = H / 2;
+        const int l = b->levels[v];
+        if (l > 0) {
+            const int W2 = c.width >> l, H2 = c.height >> l;
             LV_TRY(ensure(ctx, ctx->pyr_rgb[v][l], 3 * (size_t)W2 * H2 * 4));
             if (lsrc) LV_TRY(ensure(ctx, ctx->pyr_depth[v][l], (size_t)W2 * H2 * 4));
-            launch_pyramid_down(W, H, gsrc, lsrc, (float *)ctx->pyr_rgb[v][l].p,
-                                lsrc ? (float *)ctx->pyr_depth[v][l].p : nullptr, s);
-            gsrc = (const float *)ctx->pyr_rgb[v][l].p;
-            if (lsrc) lsrc = (const float *)ctx->pyr_depth[v][l].p;
-            W = W2;
-            H = H2;
+            PyrViews &q = pv[l];
+            const int j = q.n++;
+            q.W[j] = c.width;
+            q.H[j] = c.height;
+            q.rgb[j] = gsrc;
+            q.depth[j] = lsrc;
+            q.rgb_out[j] = (float *)ctx->pyr_rgb[v][l].p;
+            q.depth_out[j] = lsrc ? (float *)ctx->pyr_depth[v][l].p : nullptr;
+            q.base[j + 1] = q.base[j] + (uint32_t)W2 * (uint32_t)H2;
+            gsrc = q.rgb_out[j];
+            if (lsrc) lsrc = q.depth_out[j];
         }
         gt_l[v] = gsrc;
         li_l[v] = lsrc;
+    }
+    {
+        Phase ph(ctx, LVIGS_PHASE_PYRAMID, s);
+        for (int l = 1; l <= LVIGS_MAX_LEVEL; ++l) launch_pyramid_views(pv[l], l, s);
     }
     // 2. a1-a4 over all views at once
     LV_TRY(build_lists(ctx, st, s, eager, 1.3));

@@ -292,6 +292,59 @@ __global__ void pyramid_down_kernel(int W, int H, const float *__restrict__ rgb,
     }
 }
 
+// The pyramid level `L` value of pixel (x, y), evaluated from level 0 with the
+// arithmetic of L successive pyramid_down_kernel passes (same operations in
+// the same order, so the result is bit-identical).
+template <int L>
+__device__ __forceinline__ float pyr_rgb(const float *__restrict__ s, int W0, int x, int y) {
+    if constexpr (L == 0) {
+        return s[(size_t)y * W0 + x];
+    } else {
+        return 0.25f * ((pyr_rgb<L - 1>(s, W0, 2 * x, 2 * y) + pyr_rgb<L - 1>(s, W0, 2 * x + 1, 2 * y)) +
+                        (pyr_rgb<L - 1>(s, W0, 2 * x, 2 * y + 1) + pyr_rgb<L - 1>(s, W0, 2 * x + 1, 2 * y + 1)));
+    }
+}
+
+template <int L>
+__device__ __forceinline__ float pyr_depth(const float *__restrict__ d, int W0, int x, int y) {
+    if constexpr (L == 0) {
+        return d[(size_t)y * W0 + x];
+    } else {
+        const float v[4] = {pyr_depth<L - 1>(d, W0, 2 * x, 2 * y), pyr_depth<L - 1>(d, W0, 2 * x + 1, 2 * y),
+                            pyr_depth<L - 1>(d, W0, 2 * x, 2 * y + 1), pyr_depth<L - 1>(d, W0, 2 * x + 1, 2 * y + 1)};
+        float sum = 0.f;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (v[k] > 0.f) {
+                sum += v[k];
+                ++cnt;
+            }
+        return cnt ? sum / (float)cnt : 0.f;
+    }
+}
+
+// Every listed view's target at pyramid level L, straight from level 0, in
+// one launch (one instantiation per level keeps the register use of the
+// shallow levels low).
+template <int L>
+__global__ void pyramid_views_kernel(PyrViews pv) {
+    const uint32_t total = pv.base[pv.n];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int v = 0;
+        while (v + 1 < pv.n && pv.base[v + 1] <= t) ++v;
+        const int W0 = pv.W[v], H0 = pv.H[v];
+        const int Wl = W0 >> L;
+        const uint32_t i = t - pv.base[v];
+        const int x = (int)(i % (uint32_t)Wl), y = (int)(i / (uint32_t)Wl);
+        const size_t n = (size_t)Wl * (H0 >> L);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+            pv.rgb_out[v][(size_t)ch * n + i] = pyr_rgb<L>(pv.rgb[v] + (size_t)ch * W0 * H0, W0, x, y);
+        if (pv.depth[v]) pv.depth_out[v][i] = pyr_depth<L>(pv.depth[v], W0, x, y);
+    }
+}
+
 Window make_window() {
     Window w;
     double g[11], s = 0.0;
@@ -341,6 +394,20 @@ void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, flo
     int blocks = (n + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     pyramid_down_kernel<<<blocks, 256, 0, s>>>(W, H, rgb, depth, rgb_out, depth_out);
+}
+
+void launch_pyramid_views(const PyrViews &pv, int level, cudaStream_t s) {
+    const uint32_t total = pv.n > 0 ? pv.base[pv.n] : 0;
+    if (total == 0) return;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    switch (level) {
+    case 1: pyramid_views_kernel<1><<<blocks, 256, 0, s>>>(pv); break;
+    case 2: pyramid_views_kernel<2><<<blocks, 256, 0, s>>>(pv); break;
+    case 3: pyramid_views_kernel<3><<<blocks, 256, 0, s>>>(pv); break;
+    case 4: pyramid_views_kernel<4><<<blocks, 256, 0, s>>>(pv); break;
+    default: break;
+    }
 }
 
 } // namespace lvigs

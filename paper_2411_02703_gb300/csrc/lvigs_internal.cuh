@@ -212,6 +212,20 @@ void launch_loss(const LossViews &lv, void *tmp, cudaStream_t s);
 void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, float *rgb_out,
                          float *depth_out, cudaStream_t s);
 
+// Targets of several views at one pyramid level (1..4) in one launch,
+// bit-identical to repeated launch_pyramid_down.  W, H: level-0 size; base:
+// prefix of the output pixel counts.
+struct PyrViews {
+    int n;
+    int W[kMaxViews], H[kMaxViews];
+    const float *rgb[kMaxViews];
+    const float *depth[kMaxViews]; // may be null
+    float *rgb_out[kMaxViews];
+    float *depth_out[kMaxViews];
+    uint32_t base[kMaxViews + 1];
+};
+void launch_pyramid_views(const PyrViews &pv, int level, cudaStream_t s);
+
 // ---- map maintenance (map.cu) ----
 // Five parameter-shaped buffers (layouts of the Gaussian parameters).
 struct ParamBufs {
