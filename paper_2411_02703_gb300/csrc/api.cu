@@ -657,7 +657,7 @@ lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
     lv.W[0] = width;
     lv.H[0] = height;
     lv.tile_base[0] = 0;
-    lv.total_tiles = (uint32_t)(((width + 15) / 16) * ((height + 15) / 16));
+    lv.total_tiles = loss_tile_count(width, height);
     lv.rgb[0] = rgb;
     lv.depth[0] = depth;
     lv.gt[0] = gt_rgb;
@@ -871,7 +871,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         lv.W[v] = d.W;
         lv.H[v] = d.H;
         lv.tile_base[v] = ltiles;
-        ltiles += (uint32_t)(((d.W + 15) / 16) * ((d.H + 15) / 16));
+        ltiles += loss_tile_count(d.W, d.H);
         lv.rgb[v] = im.rgb[v];
         lv.depth[v] = im.depth[v];
         lv.gt[v] = gt_l[v];

@@ -26,8 +26,8 @@ namespace {
 
 // Worst case of loss_tmp_bytes over images with at most
 // LVIGS_LOSS_NOALLOC_MAX_PIXELS pixels and at most LVIGS_LOSS_NOALLOC_MAX_SIDE
-// pixels per side is 11,840,960 bytes (164 x 1998: the derivative maps, 9
-// floats a pixel, plus 32 bytes for each of 1375 16x16 tiles); 12 MiB covers it.
+// pixels per side is 11,809,056 bytes (164 x 1998: the derivative maps, 9
+// floats a pixel, plus 32 bytes for each of 378 32x32 tiles); 12 MiB covers it.
 constexpr size_t kScratchBytes = size_t(12) << 20;
 constexpr int kMaxDevices = 64;
 
@@ -80,7 +80,7 @@ extern "C" lvigs_status lvigs_loss_noalloc(int width, int height, const float *r
     lv.W[0] = width;
     lv.H[0] = height;
     lv.tile_base[0] = 0;
-    lv.total_tiles = (uint32_t)(((width + 15) / 16) * ((height + 15) / 16));
+    lv.total_tiles = loss_tile_count(width, height);
     lv.rgb[0] = rgb;
     lv.depth[0] = depth;
     lv.gt[0] = gt_rgb;

@@ -191,10 +191,15 @@ void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 
                           GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);
 
 // Loss (Eq. 10-12) over one or more views (packed per view through the arrays).
+// The loss kernels work on square tiles of kLossTile pixels.
+constexpr int kLossTile = 32;
+inline uint32_t loss_tile_count(int W, int H) {
+    return (uint32_t)(((W + kLossTile - 1) / kLossTile) * ((H + kLossTile - 1) / kLossTile));
+}
 struct LossViews {
     int n_views;
     int W[kMaxViews], H[kMaxViews];
-    uint32_t tile_base[kMaxViews]; // first 16x16 loss tile of each view
+    uint32_t tile_base[kMaxViews]; // first loss tile of each view
     uint32_t total_tiles;
     const float *rgb[kMaxViews];
     const float *depth[kMaxViews];
