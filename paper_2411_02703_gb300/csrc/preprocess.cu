@@ -1,6 +1,7 @@
 // preprocess.cu -- per-Gaussian projection (a1) and its chain rule (a7).
 //
-// Forward, one thread per Gaussian looping over the views of the call:
+// Forward, one warp per 32 Gaussians (the pairs in front of the near plane
+// dealt out over the lanes), for every view of the call:
 //   Sigma = R S S^T R^T (Eq. 2), the EWA projection Sigma_I = J Q Sigma Q^T J^T
 //   and mu_I = [Q, T] mu (Eq. 7), the 0.3 px^2 dilation, the conic, the 3-sigma
 //   radius and tile rectangle, opacity = sigmoid(logit) and the SH colour.
@@ -179,45 +180,156 @@ __device__ __forceinline__ float sig(const float S[6], int i, int j) {
     return S[lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)];
 }
 
-__global__ void __launch_bounds__(128)
+constexpr int kShRow = 48;   // 16 coefficients x 3 channels
+constexpr int kShPitch = 49; // staged row pitch: odd, so lanes reading 32 rows hit 32 banks
+
+// A warp's 32 consecutive SH rows (one contiguous run of nrows * row floats)
+// into dst at pitch kShPitch: float4 loads all issued before the stores when
+// the run is 16-byte aligned.  row <= kShRow.
+__device__ __forceinline__ void stage_sh_rows(const float *__restrict__ src, int nrows, int row, int lane,
+                                              float *__restrict__ dst) {
+    const int n = nrows * row;
+    if ((((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
+        constexpr int kMaxIt = 32 * kShRow / 4 / 32;
+        float4 v[kMaxIt];
+#pragma unroll
+        for (int i = 0; i < kMaxIt; ++i) {
+            const int e4 = lane + 32 * i;
+            if (4 * e4 < n) v[i] = __ldg(reinterpret_cast<const float4 *>(src) + e4);
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxIt; ++i) {
+            const int e = 4 * (lane + 32 * i);
+            if (e < n) {
+                const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int rr = (e + c) / row, cc = (e + c) - rr * row;
+                    dst[rr * kShPitch + cc] = f[c];
+                }
+            }
+        }
+    } else {
+        for (int e = lane; e < n; e += 32) {
+            const int rr = e / row, cc = e - rr * row;
+            dst[rr * kShPitch + cc] = __ldg(src + e);
+        }
+    }
+}
+
+// mu_I = [Q_iw, T_iw] mu_W (Eq. 7), strict binary32.
+__device__ __forceinline__ void view_point_strict(const ViewDesc &V, float mx, float my, float mz, float &px,
+                                                  float &py, float &pz) {
+    px = RN_MUL(V.R[0], mx);
+    px = RN_ADD(px, RN_MUL(V.R[1], my));
+    px = RN_ADD(px, RN_MUL(V.R[2], mz));
+    px = RN_ADD(px, V.t[0]);
+    py = RN_MUL(V.R[3], mx);
+    py = RN_ADD(py, RN_MUL(V.R[4], my));
+    py = RN_ADD(py, RN_MUL(V.R[5], mz));
+    py = RN_ADD(py, V.t[1]);
+    pz = RN_MUL(V.R[6], mx);
+    pz = RN_ADD(pz, RN_MUL(V.R[7], my));
+    pz = RN_ADD(pz, RN_MUL(V.R[8], mz));
+    pz = RN_ADD(pz, V.t[2]);
+}
+
+// Forward (a1).  A warp owns 32 consecutive Gaussians.  Every lane first
+// projects its Gaussian's mean into every view (depth key bits for all pairs);
+// the pairs in front of the near plane are then dealt out over all 32 lanes
+// for the projected covariance, radius, tile rectangle, SH colour and record,
+// the worker taking the owner's mean, Sigma and opacity by shuffle and its SH
+// row from shared memory (staged with coalesced loads).
+constexpr int kFwdThreads = 128;
+
+__global__ void __launch_bounds__(kFwdThreads)
 preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__restrict__ recs,
                       uint32_t *__restrict__ tiles, uint32_t *__restrict__ zbits,
                       uint2 *__restrict__ rects) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.n) return;
-    const size_t N = (size_t)P.n;
-    GaussLocal L;
-    gauss_local_strict(P, g, L);
-    const float mx = P.means[3 * (size_t)g], my = P.means[3 * (size_t)g + 1],
-                mz = P.means[3 * (size_t)g + 2];
-    const float opacity = 1.f / (1.f + expf(-P.opacity_logits[g]));
+    __shared__ float s_sh[kFwdThreads / 32][32 * kShPitch];
+    __shared__ uint32_t s_mask[kFwdThreads / 32][kMaxViews];
+    __shared__ int s_pref[kFwdThreads / 32][kMaxViews + 1];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t N = P.n;
+    const int64_t g0 = (int64_t)blockIdx.x * kFwdThreads + (tid & ~31);
+    const int64_t g = g0 + lane;
+    const bool valid = g < N;
+    const int nrows = (int)(N - g0 < 32 ? N - g0 : 32);
+    if (nrows <= 0) return; // whole warp past the end (warp-uniform)
     const int deg = P.sh_degree;
     const int nk = (deg + 1) * (deg + 1);
-    const float *shg = P.sh + (size_t)g * P.sh_stride_k * 3;
+    const int row = P.sh_stride_k * 3;
+    const bool staged = row <= kShRow;
+    if (staged) stage_sh_rows(P.sh + g0 * row, nrows, row, lane, s_sh[w]);
+
+    GaussLocal L;
+    L.ok = false;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) L.S[i] = 0.f;
+    float mx = 0.f, my = 0.f, mz = 0.f, opacity = 0.f;
+    if (valid) {
+        gauss_local_strict(P, (int)g, L);
+        mx = P.means[3 * g];
+        my = P.means[3 * g + 1];
+        mz = P.means[3 * g + 2];
+        opacity = 1.f / (1.f + expf(-P.opacity_logits[g]));
+    }
     const float tw = (float)vsp->tile_w, th = (float)vsp->tile_h;
     const int n_views = vsp->n_views;
 
-#pragma unroll 1
+    // depth key of every pair; pairs in front of the near plane go on to the rest
     for (int vi = 0; vi < n_views; ++vi) {
+        bool front = false;
+        if (valid) {
+            const size_t o = (size_t)vi * N + g;
+            float px, py, pz;
+            view_point_strict(vsp->v[vi], mx, my, mz, px, py, pz);
+            front = L.ok && (pz > 0.2f);
+            zbits[o] = __float_as_uint(pz);
+            if (!front) {
+                tiles[o] = 0;
+                rects[o] = make_uint2(0, 0);
+            }
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, front);
+        if (lane == 0) s_mask[w][vi] = m;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        int acc = 0;
+        for (int vi = 0; vi < n_views; ++vi) {
+            s_pref[w][vi] = acc;
+            acc += __popc(s_mask[w][vi]);
+        }
+        s_pref[w][n_views] = acc;
+    }
+    __syncwarp();
+    const int total = s_pref[w][n_views];
+
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        const bool has = p < total;
+        int vi = 0, src = lane;
+        if (has) {
+            while (vi + 1 < n_views && s_pref[w][vi + 1] <= p) ++vi;
+            src = (int)__fns(s_mask[w][vi], 0, p - s_pref[w][vi] + 1);
+        }
+        const float gx = __shfl_sync(0xffffffffu, mx, src);
+        const float gy = __shfl_sync(0xffffffffu, my, src);
+        const float gz = __shfl_sync(0xffffffffu, mz, src);
+        const float op = __shfl_sync(0xffffffffu, opacity, src);
+        float S[6];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) S[t] = __shfl_sync(0xffffffffu, L.S[t], src);
+        if (!has) continue;
         const ViewDesc &V = vsp->v[vi];
-        const size_t o = (size_t)vi * N + g;
-        // mu_I = [Q_iw, T_iw] mu_W  (Eq. 7), strict
-        float px = RN_MUL(V.R[0], mx);
-        px = RN_ADD(px, RN_MUL(V.R[1], my));
-        px = RN_ADD(px, RN_MUL(V.R[2], mz));
-        px = RN_ADD(px, V.t[0]);
-        float py = RN_MUL(V.R[3], mx);
-        py = RN_ADD(py, RN_MUL(V.R[4], my));
-        py = RN_ADD(py, RN_MUL(V.R[5], mz));
-        py = RN_ADD(py, V.t[1]);
-        float pz = RN_MUL(V.R[6], mx);
-        pz = RN_ADD(pz, RN_MUL(V.R[7], my));
-        pz = RN_ADD(pz, RN_MUL(V.R[8], mz));
-        pz = RN_ADD(pz, V.t[2]);
-        bool vis = L.ok && (pz > 0.2f);
+        const size_t o = (size_t)vi * N + (size_t)(g0 + src);
+        float px, py, pz;
+        view_point_strict(V, gx, gy, gz, px, py, pz);
+        bool vis = true;
         float a = 0.f, b = 0.f, c = 0.f, det = 0.f, u = 0.f, v = 0.f;
         int rad = 0;
-        if (vis) {
+        {
             const float xz = RN_DIV(px, pz), yz = RN_DIV(py, pz);
             const float txc = xz < -V.limx ? -V.limx : (xz > V.limx ? V.limx : xz);
             const float tyc = yz < -V.limy ? -V.limy : (yz > V.limy ? V.limy : yz);
@@ -236,9 +348,9 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    float acc = RN_MUL(T[3 * i], sig(L.S, 0, j));
-                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 1], sig(L.S, 1, j)));
-                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 2], sig(L.S, 2, j)));
+                    float acc = RN_MUL(T[3 * i], sig(S, 0, j));
+                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 1], sig(S, 1, j)));
+                    acc = RN_ADD(acc, RN_MUL(T[3 * i + 2], sig(S, 2, j)));
                     U[3 * i + j] = acc;
                 }
             a = dot3_strict(U[0], U[1], U[2], T[0], T[1], T[2]);
@@ -269,34 +381,34 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
             rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
         }
         tiles[o] = ntiles;
-        zbits[o] = __float_as_uint(pz);
         rects[o] = rect;
         if (ntiles == 0) continue;
         // values composited (binary32; not part of the key)
         const float inv_det = 1.f / det;
         // colour: SH at the direction from the camera centre to the mean
-        float dx = mx - V.campos[0], dy = my - V.campos[1], dz = mz - V.campos[2];
+        float dx = gx - V.campos[0], dy = gy - V.campos[1], dz = gz - V.campos[2];
         const float inv_len = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= inv_len;
         dy *= inv_len;
         dz *= inv_len;
         float Y[16];
         sh_values(deg, dx, dy, dz, Y);
+        const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
         float rgb[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.5f;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
-                if (k < nk) acc += Y[k] * __ldg(shg + 3 * k + ch);
+                if (k < nk) acc += Y[k] * shg[3 * k + ch];
             rgb[ch] = fmaxf(acc, 0.f);
         }
         // half-extents of the box where o exp(power) can reach 1/255: the
         // ellipse d^T Sigma_I^{-1} d <= 2 (ln(255 o) + 0.1), widened by 0.05 px;
         // the margin is far above the binary32 rounding of the compositing test
         float ex = -1e30f, ey = -1e30f;
-        if (opacity * 255.f >= 1.f) {
-            const float tau = logf(255.f * opacity) + 0.1f;
+        if (op * 255.f >= 1.f) {
+            const float tau = logf(255.f * op) + 0.1f;
             ex = (a > 0.f) ? sqrtf(2.f * tau * a) + 0.05f : 1e30f;
             ey = (c > 0.f) ? sqrtf(2.f * tau * c) + 0.05f : 1e30f;
         }
@@ -305,7 +417,7 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
         constexpr float kLog2e = 1.4426950408889634f;
         GRec rec;
         rec.a = make_float4(u, v, (c * inv_det) * (-0.5f * kLog2e), (b * inv_det) * kLog2e);
-        rec.b = make_float4((a * inv_det) * (-0.5f * kLog2e), opacity, pz, ex);
+        rec.b = make_float4((a * inv_det) * (-0.5f * kLog2e), op, pz, ex);
         rec.c = make_float4(rgb[0], rgb[1], rgb[2], ey);
         recs[o] = rec;
     }
@@ -326,8 +438,6 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
 // ---------------------------------------------------------------------------
 constexpr int kBwdThreads = 128;
 constexpr int kAccScalars = 10; // d_mean 3, dSigma 6 (00,01,02,11,12,22), d_opacity 1
-constexpr int kShRow = 48;      // 16 coefficients x 3 channels
-constexpr int kShPitch = 49;    // staged row pitch: odd, so lanes reading 32 rows hit 32 banks
 constexpr size_t kBwdSmem = sizeof(float) * ((kAccScalars + kShRow) * (kBwdThreads + 1) + kBwdThreads * kShPitch) +
                             sizeof(uint32_t) * (kBwdThreads / 32) * kMaxViews +
                             sizeof(int) * (kBwdThreads / 32) * (kMaxViews + 1);
@@ -356,38 +466,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
 
 #pragma unroll
     for (int k = 0; k < kAccScalars + kShRow; ++k) s_acc[k][tid] = 0.f;
-    if (staged) {
-        // the warp's rows are one contiguous run: float4 loads, all issued before the stores
-        const float *src = P.sh + g0 * row;
-        const int n = nrows * row;
-        // (rows land at an odd pitch in shared memory)
-        if ((((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
-            constexpr int kMaxIt = 32 * kShRow / 4 / 32;
-            float4 v[kMaxIt];
-#pragma unroll
-            for (int i = 0; i < kMaxIt; ++i) {
-                const int e4 = lane + 32 * i;
-                if (4 * e4 < n) v[i] = __ldg(reinterpret_cast<const float4 *>(src) + e4);
-            }
-#pragma unroll
-            for (int i = 0; i < kMaxIt; ++i) {
-                const int e = 4 * (lane + 32 * i);
-                if (e < n) {
-                    const float f[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int rr = (e + c) / row, cc = (e + c) - rr * row;
-                        s_sh[w][rr * kShPitch + cc] = f[c];
-                    }
-                }
-            }
-        } else {
-            for (int e = lane; e < n; e += 32) {
-                const int rr = e / row, cc = e - rr * row;
-                s_sh[w][rr * kShPitch + cc] = __ldg(src + e);
-            }
-        }
-    }
+    if (staged) stage_sh_rows(P.sh + g0 * row, nrows, row, lane, s_sh[w]);
 
     // per-Gaussian forward quantities
     float mx = 0.f, my = 0.f, mz = 0.f, s[3] = {1.f, 1.f, 1.f}, r[9], M[9], Sg6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -681,9 +760,8 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
 void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs, GRec *recs, uint32_t *tiles,
                            uint32_t *zbits, uint2 *rects, cudaStream_t s) {
     if (P.n <= 0) return;
-    const int threads = 128;
-    const int blocks = (P.n + threads - 1) / threads;
-    preprocess_fwd_kernel<<<blocks, threads, 0, s>>>(P, vs, recs, tiles, zbits, rects);
+    const int blocks = (P.n + kFwdThreads - 1) / kFwdThreads;
+    preprocess_fwd_kernel<<<blocks, kFwdThreads, 0, s>>>(P, vs, recs, tiles, zbits, rects);
 }
 
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs, const uint32_t *tiles,
