@@ -153,13 +153,21 @@ radix_upsweep_kernel(const uint32_t *keys, const uint32_t *n_dev, uint32_t n_hos
     uint32_t begin, end;
     rs_chunk(n, G, blockIdx.x, begin, end);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t i0 = begin + warp * 32; i0 < end; i0 += kRsThreads) {
-        const uint32_t i = i0 + lane;
-        const bool valid = i < end;
-        const uint32_t d = valid ? (keys[i] >> shift) & 255u : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (valid && lane == __ffs(peers) - 1) hist[warp][d] += __popc(peers);
-        __syncwarp();
+    // kRsItems keys per lane and round, all loaded before the first is counted;
+    // within an instruction the leaders of a digit's peers hit distinct bins
+    for (uint32_t i0 = begin + warp * (32 * kRsItems); i0 < end; i0 += kRsThreads * kRsItems) {
+        uint32_t d[kRsItems];
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t i = i0 + j * 32 + lane;
+            d[j] = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
+            if (d[j] < 256u && lane == __ffs(peers) - 1) hist[warp][d[j]] += __popc(peers);
+            __syncwarp();
+        }
     }
     __syncthreads();
     const int d = threadIdx.x;
@@ -207,6 +215,8 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_hist[kRsWarps][256];
     __shared__ uint32_t s_tile[256];
+    __shared__ uint32_t s_start[256];          // first position of each digit in the tile
+    __shared__ uint32_t s_k[kRsTile], s_v[kRsTile]; // the tile in digit order
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     {
         uint32_t tot;
@@ -241,6 +251,7 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
             __syncwarp();
         }
         __syncthreads();
+        uint32_t tile_n;
         {
             uint32_t run = 0;
 #pragma unroll
@@ -250,14 +261,29 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
                 run += c;
             }
             s_tile[t] = run;
+            s_start[t] = block_exclusive_scan_256(run, &tile_n);
         }
         __syncthreads();
+        // reorder the tile by digit in shared memory (stable) ...
 #pragma unroll
         for (int j = 0; j < kRsItems; ++j) {
             if (d[j] < 256u) {
-                const uint32_t dest = s_base[d[j]] + s_hist[warp][d[j]] + rank[j];
-                keys_out[dest] = k[j];
-                vals_out[dest] = v[j];
+                const uint32_t lp = s_start[d[j]] + s_hist[warp][d[j]] + rank[j];
+                s_k[lp] = k[j];
+                s_v[lp] = v[j];
+            }
+        }
+        __syncthreads();
+        // ... and write it out: consecutive threads, consecutive addresses within a digit's run
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t lp = (uint32_t)(j * kRsThreads + t);
+            if (lp < tile_n) {
+                const uint32_t key = s_k[lp];
+                const uint32_t dg = (key >> shift) & 255u;
+                const uint32_t dest = s_base[dg] + (lp - s_start[dg]);
+                keys_out[dest] = key;
+                vals_out[dest] = s_v[lp];
             }
         }
         __syncthreads();
