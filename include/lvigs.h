@@ -239,6 +239,11 @@ lvigs_status lvigs_debug_keys(lvigs_ctx *ctx, int view_slot, uint64_t *keys, uin
 lvigs_status lvigs_debug_state(lvigs_ctx *ctx, int view_slot, uint32_t *ranges, int32_t *n_contrib,
                                float *final_T, int *n_tiles, void *stream);
 
+/* Parity hook: y[i] = exp(x[i]) rounded once to binary32 as the key stage
+ * computes the scales (the value of exp in binary64, rounded; Sec. III-E
+ * scale activation), for n device floats. */
+lvigs_status lvigs_debug_exp_key(const float *x, float *y, int64_t n, void *stream);
+
 /* Wait for `stream` and return any error latched on the device since the
  * last call (capacity overflow, bounded-wait timeout), clearing it. */
 lvigs_status lvigs_sync_status(lvigs_ctx *ctx, void *stream);

@@ -64,6 +64,14 @@ def _load():
     return _lib
 
 
+def exp_key(x):
+    """The key stage's scale exp: (float)exp((double)x) per element (C libm)."""
+    xs = np.ascontiguousarray(x, np.float32)
+    y = np.empty_like(xs)
+    _load().orc_exp_key(_p(xs), _p(y), ctypes.c_int64(xs.size))
+    return y
+
+
 def num_threads() -> int:
     return int(_load().orc_num_threads())
 

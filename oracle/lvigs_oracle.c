@@ -46,6 +46,12 @@ typedef struct {
     int W, H;
 } orc_camera;
 
+/* The key stage's scale: exp of the binary32 log-scale in binary64, rounded
+ * once to binary32 (reading R1 of the scale activation). */
+void orc_exp_key(const float *x, float *y, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) y[i] = (float)exp((double)x[i]);
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

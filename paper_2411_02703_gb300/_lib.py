@@ -96,6 +96,7 @@ SIGNATURES = {
     "lvigs_train_step_batched": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Batch), ctypes.POINTER(Grads), _P]),
     "lvigs_debug_keys": (_I, [_P, _I, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
     "lvigs_debug_state": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
+    "lvigs_debug_exp_key": (_I, [_P, _P, ctypes.c_int64, _P]),
     "lvigs_sync_status": (_I, [_P, _P]),
     "lvigs_release_view": (_I, [_P, _I]),
     "lvigs_last_error": (ctypes.c_char_p, [_P]),

@@ -697,6 +697,12 @@ lvigs_status lvigs_debug_keys(lvigs_ctx *ctx, int view_slot, uint64_t *keys, uin
     return LVIGS_OK;
 }
 
+lvigs_status lvigs_debug_exp_key(const float *x, float *y, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return LVIGS_ERR_INVALID_ARG;
+    launch_exp_key(x, y, n, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? LVIGS_OK : LVIGS_ERR_CUDA;
+}
+
 lvigs_status lvigs_debug_state(lvigs_ctx *ctx, int view_slot, uint32_t *ranges, int32_t *n_contrib,
                                float *final_T, int *n_tiles, void *stream) {
     if (!ctx) return LVIGS_ERR_INVALID_ARG;

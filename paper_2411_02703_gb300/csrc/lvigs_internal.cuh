@@ -115,6 +115,15 @@ namespace lvigs {
 
 // ViewSet pointers passed to kernels are DEVICE copies; the host copy (by
 // reference) is only used to size grids.
+// Table and constants of the key stage's binary32 exponential.
+struct ExpKeyTable {
+    float hi[32], lo[32]; // 2^(j/32) = hi + lo
+    float inv_step;       // 32 / ln 2
+    float c1, c2, c3;     // ln2 / 32 = c1 + c2 + c3 (c1, c2: 12 significant bits)
+};
+// y[i] = (float)exp((double)x[i]) as the key stage evaluates it (parity hook).
+void launch_exp_key(const float *x, float *y, int64_t n, cudaStream_t s);
+
 void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs_dev, GRec *recs, uint32_t *tiles,
                            uint32_t *zbits, uint2 *rects, cudaStream_t s);
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs_dev, const uint32_t *tiles,

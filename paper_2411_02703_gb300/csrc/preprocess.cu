@@ -13,6 +13,8 @@
 // Backward, one warp per 32 Gaussians: the visible (view, Gaussian) pairs are
 // dealt out over the lanes and summed per Gaussian in shared memory, so the
 // parameter gradients need no global atomics.
+#include <cmath>
+
 #include "lvigs_internal.cuh"
 
 namespace lvigs {
@@ -131,6 +133,55 @@ __device__ __forceinline__ float tile_coord(float f, int hi) {
     return f;
 }
 
+// exp(x) rounded once to binary32, the value (float)exp((double)x) of the key
+// stage, without binary64 arithmetic on the common path (binary64 runs at a
+// small fraction of the binary32 rate on this GPU).  Tang's table-driven
+// reduction: x = (32 m + j) ln2/32 + r, |r| <= ln2/64, with ln2/32 split in
+// three parts (the first two of 12 significant bits, so k times each is exact)
+// and r kept as a normalised float pair; exp(r) - 1 = r + r^2/2 + r^3/6 + r^4/24 (the
+// truncation is below 2^-39); 2^(j/32) is a float pair from the table; the
+// products and sums that matter are exact (FMA products, two-sums).  The
+// result y = z + d (z the nearest float) is within about 2^-36 relative of
+// exp(x); when the rounding of z is not certain by a margin of 1e-10 z (the
+// exact value may lie across a rounding boundary), or |x| >= 60, the binary64
+// path decides.  So the result is always the binary64 path's.
+__device__ __forceinline__ float exp_key(float x, const ExpKeyTable &t) {
+    if (!(fabsf(x) < 60.f)) return __double2float_rn(exp((double)x));
+    // (explicitly rounded operations: none of the exact steps may be contracted)
+    const float kf = rintf(RN_MUL(x, t.inv_step));
+    const int k = (int)kf;
+    const int j = k & 31, m = k >> 5;
+    // r = x - k ln2/32 = rh + rl
+    const float r1 = __fmaf_rn(-kf, t.c1, x); // exact
+    const float p2 = RN_MUL(kf, t.c2);         // exact
+    const float r2 = RN_SUB(r1, p2);
+    const float bv = RN_SUB(r2, r1);
+    const float er = RN_ADD(RN_SUB(r1, RN_SUB(r2, bv)), RN_SUB(-p2, bv)); // two-sum error
+    const float r3 = __fmaf_rn(-kf, t.c3, er); // up to about 1e-6: renormalise the pair
+    const float rh = RN_ADD(r2, r3);
+    const float bu = RN_SUB(rh, r2);
+    const float rl = RN_ADD(RN_SUB(r2, RN_SUB(rh, bu)), RN_SUB(r3, bu));
+    const float q = RN_MUL(RN_MUL(rh, rh), __fmaf_rn(rh, __fmaf_rn(rh, 1.f / 24.f, 1.f / 6.f), 0.5f));
+    const float pl = RN_ADD(rl, q); // exp(r) = 1 + rh + pl
+    // y = 2^(j/32) (1 + rh + pl), 2^(j/32) = th + tl
+    const float th = t.hi[j], tl = t.lo[j];
+    const float pr = RN_MUL(th, rh);
+    const float pe = __fmaf_rn(th, rh, -pr); // exact product error
+    const float yh = RN_ADD(th, pr);
+    const float bw = RN_SUB(yh, th);
+    const float e2 = RN_ADD(RN_SUB(th, RN_SUB(yh, bw)), RN_SUB(pr, bw));
+    // the rest of (th + tl)(1 + rh + pl): th pl + tl (1 + rh) (tl pl is below 2^-39)
+    const float yl = RN_ADD(RN_ADD(e2, pe), __fmaf_rn(th, pl, __fmaf_rn(tl, rh, tl)));
+    const float z = RN_ADD(yh, yl);
+    const float d = RN_ADD(RN_SUB(yh, z), yl);
+    const uint32_t zb = __float_as_uint(z);
+    const float u = RN_SUB(__uint_as_float(zb + 1u), z);
+    const bool pow2 = (zb & 0x7fffffu) == 0u;
+    const float room = d >= 0.f ? RN_SUB(RN_MUL(0.5f, u), d) : RN_ADD(RN_MUL(pow2 ? 0.25f : 0.5f, u), d);
+    if (!(room > RN_MUL(1e-10f, z))) return __double2float_rn(exp((double)x));
+    return ldexpf(z, m);
+}
+
 // Per-Gaussian, view-independent part: scales, unit quaternion, Sigma (strict).
 struct GaussLocal {
     float s[3];
@@ -141,13 +192,14 @@ struct GaussLocal {
     bool ok;
 };
 
-__device__ __forceinline__ void gauss_local_strict(const GaussParams &P, int g, GaussLocal &L) {
+__device__ __forceinline__ void gauss_local_strict(const GaussParams &P, int g, GaussLocal &L,
+                                                   const ExpKeyTable &et) {
     const float *ls = P.log_scales + 3 * (size_t)g;
     const float *q = P.quats + 4 * (size_t)g;
-    // exp in binary64, one rounding to binary32
-    L.s[0] = __double2float_rn(exp((double)ls[0]));
-    L.s[1] = __double2float_rn(exp((double)ls[1]));
-    L.s[2] = __double2float_rn(exp((double)ls[2]));
+    // exp as in binary64, one rounding to binary32
+    L.s[0] = exp_key(ls[0], et);
+    L.s[1] = exp_key(ls[1], et);
+    L.s[2] = exp_key(ls[2], et);
     const float q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
     float n2 = RN_MUL(q0, q0);
     n2 = RN_ADD(n2, RN_MUL(q1, q1));
@@ -245,8 +297,20 @@ constexpr int kFwdThreads = 128;
 __global__ void __launch_bounds__(kFwdThreads)
 preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__restrict__ recs,
                       uint32_t *__restrict__ tiles, uint32_t *__restrict__ zbits,
-                      uint2 *__restrict__ rects) {
+                      uint2 *__restrict__ rects, ExpKeyTable et_param) {
     __shared__ float s_sh[kFwdThreads / 32][32 * kShPitch];
+    __shared__ ExpKeyTable et;
+    if (threadIdx.x < 32) {
+        et.hi[threadIdx.x] = et_param.hi[threadIdx.x];
+        et.lo[threadIdx.x] = et_param.lo[threadIdx.x];
+    }
+    if (threadIdx.x == 0) {
+        et.inv_step = et_param.inv_step;
+        et.c1 = et_param.c1;
+        et.c2 = et_param.c2;
+        et.c3 = et_param.c3;
+    }
+    __syncthreads();
     __shared__ uint32_t s_mask[kFwdThreads / 32][kMaxViews];
     __shared__ int s_pref[kFwdThreads / 32][kMaxViews + 1];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -268,7 +332,7 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
     for (int i = 0; i < 6; ++i) L.S[i] = 0.f;
     float mx = 0.f, my = 0.f, mz = 0.f, opacity = 0.f;
     if (valid) {
-        gauss_local_strict(P, (int)g, L);
+        gauss_local_strict(P, (int)g, L, et);
         mx = P.means[3 * g];
         my = P.means[3 * g + 1];
         mz = P.means[3 * g + 2];
@@ -755,13 +819,52 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
     }
 }
 
+__global__ void exp_key_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t n, ExpKeyTable t) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = exp_key(x[i], t);
+}
+
+// Table and constants of exp_key, from binary64 host arithmetic.
+ExpKeyTable make_exp_key_table() {
+    ExpKeyTable t;
+    for (int j = 0; j < 32; ++j) {
+        const double v = std::exp2(j / 32.0);
+        t.hi[j] = (float)v;
+        t.lo[j] = (float)(v - (double)t.hi[j]);
+    }
+    const double step = std::log(2.0) / 32.0;
+    auto trunc12 = [](double v) {
+        int e = 0;
+        const double m = std::frexp(v, &e);
+        return std::ldexp(std::floor(std::ldexp(m, 12)), e - 12);
+    };
+    const double c1 = trunc12(step), c2 = trunc12(step - c1);
+    t.inv_step = (float)(1.0 / step);
+    t.c1 = (float)c1;
+    t.c2 = (float)c2;
+    t.c3 = (float)(step - c1 - c2);
+    return t;
+}
+
+const ExpKeyTable &exp_key_table() {
+    static const ExpKeyTable t = make_exp_key_table();
+    return t;
+}
+
 } // namespace
+
+void launch_exp_key(const float *x, float *y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    exp_key_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, y, n, exp_key_table());
+}
 
 void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs, GRec *recs, uint32_t *tiles,
                            uint32_t *zbits, uint2 *rects, cudaStream_t s) {
     if (P.n <= 0) return;
     const int blocks = (P.n + kFwdThreads - 1) / kFwdThreads;
-    preprocess_fwd_kernel<<<blocks, kFwdThreads, 0, s>>>(P, vs, recs, tiles, zbits, rects);
+    preprocess_fwd_kernel<<<blocks, kFwdThreads, 0, s>>>(P, vs, recs, tiles, zbits, rects, exp_key_table());
 }
 
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs, const uint32_t *tiles,

@@ -128,6 +128,35 @@ def test_keys_bit_exact_full_size_lidar(pkg):
             np.testing.assert_array_equal(vals.cpu().numpy().view(np.uint32), rv)
 
 
+def test_key_exp_bit_exact(pkg):
+    """The key stage's binary32 exp (table-driven, binary64 only where the
+    rounding is not certain) against the oracle's binary64 exp rounded once:
+    16.8M values over the log-scale range, the reduction's boundaries, the
+    fallback range and special values."""
+    import ctypes
+
+    from paper_2411_02703_gb300 import _lib as L
+
+    rng = np.random.default_rng(5)
+    step = np.log(2.0) / 32.0
+    k = np.arange(-2000, 2000)
+    edges = np.concatenate([(k + 0.5) * step, k * step])
+    x = np.concatenate([rng.uniform(-12, 8, 12_000_000), rng.normal(-3, 0.5, 4_000_000),
+                        edges, np.nextafter(edges.astype(np.float32), np.float32(np.inf)),
+                        np.nextafter(edges.astype(np.float32), np.float32(-np.inf)),
+                        rng.uniform(-90, 90, 100_000),
+                        [0.0, -0.0, 1e-30, -1e-30, 59.999, -59.999, 60.0, -60.0, 88.7, -103.0]]).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    code = L.load().lvigs_debug_exp_key(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), x.size,
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 0
+    ref = O.exp_key(x)
+    got = yd.cpu().numpy()
+    bad = np.nonzero(got.view(np.uint32) != ref.view(np.uint32))[0]
+    assert bad.size == 0, (bad.size, x[bad[:5]], got[bad[:5]], ref[bad[:5]])
+
+
 def test_ranges_and_contributors(pkg):
     params, spec, _, _ = S.small_scene()
     lv = ctx_for(pkg)

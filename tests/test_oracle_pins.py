@@ -485,3 +485,13 @@ def test_backward_matches_central_fd():
                 n_checked += 1
     # a perturbation that flips any threshold test anywhere in the image is skipped
     assert n_checked > 900 and n_skipped < 0.1 * (n_checked + n_skipped)
+
+
+def test_exp_key_is_binary64_exp_rounded_once():
+    """The key stage's scale: numpy's binary64 exp rounded to binary32 is an
+    independent evaluation of the same definition."""
+    rng = np.random.default_rng(21)
+    x = np.concatenate([rng.uniform(-12, 8, 1_000_000), rng.normal(-3, 0.5, 200_000),
+                        [0.0, -0.0, 1e-30, -1e-30, 59.9, -59.9, 88.0, -100.0]]).astype(np.float32)
+    ref = np.exp(x.astype(np.float64)).astype(np.float32)
+    np.testing.assert_array_equal(O.exp_key(x), ref)
