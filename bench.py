@@ -133,6 +133,35 @@ def algorithmic_bytes(N, V, K, n_vis, M, P, loaded, pyr_px=0):
     }
 
 
+# Kernel source file of each profiled phase: the DRAM traffic recorded from an
+# ncu capture is reported only while that file is unchanged since the capture.
+PHASE_SOURCE = {"composite_fwd": "composite.cu", "composite_bwd": "composite.cu", "combine": "composite.cu",
+                "preprocess": "preprocess.cu", "preprocess_bwd": "preprocess.cu", "loss": "loss.cu", "adam": "map.cu"}
+
+
+def recorded_traffic(phase):
+    """DRAM bytes per launch of the phase's kernel from profiles/dram_traffic.md
+    (lines `phase kernel source_sha256 bytes_per_launch workload`), or None
+    when no capture matches the current source."""
+    import hashlib
+
+    src = PHASE_SOURCE.get(phase)
+    if src is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, "paper_2411_02703_gb300", "csrc", src), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.md")) as f:
+            for line in f:
+                parts = line.strip().strip("|").split("|")
+                parts = [x.strip() for x in parts]
+                if len(parts) >= 5 and parts[0] == phase and parts[2] == sha:
+                    return float(parts[3])
+    except OSError:
+        return None
+    return None
+
+
 def alu_flops(n_contrib_sum):
     # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernel
     # source (an FMA counts 2): forward 20 (offset, quadratic form 7, exp 2,
@@ -296,13 +325,13 @@ def run_ours(args):
         alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": flops[dominant] / t_dom / 1e12,
                 "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": None,
+                "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": recorded_traffic(dominant),
                 "peak_source": "152 SM x 128 FP32 lanes x 2 x sm_max_mhz",
                 "hbm_achieved_gbs": ab[dominant] / t_dom / 1e9}
     else:
         ach = ab[dominant] / t_dom / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind}
+                "frac": ach / hbm_peak, "traffic": recorded_traffic(dominant), "peak_source": peak_kind}
 
     steps_per_s = 1000.0 / ms_batched
     value = world * steps_per_s
@@ -395,7 +424,7 @@ def time_map_ops(P, S, lv, params, grads, cam, stream, hbm_peak, peak_kind):
     removed = gm.prune(lv, 0.005)
     torch.cuda.synchronize()
     ms_prune = (time.perf_counter() - t0) * 1e3
-    return {"adam": {"ms": round(ms_adam, 4), "bytes": adam_bytes,
+    return {"adam": {"ms": round(ms_adam, 4), "bytes": adam_bytes, "traffic": recorded_traffic("adam"),
                      "achieved_gbs": round(adam_bytes / ms_adam / 1e6, 1),
                      "frac": round(adam_bytes / ms_adam / 1e6 / hbm_peak, 3), "peak": hbm_peak,
                      "peak_source": peak_kind, "floats": N * (11 + 3 * K)},

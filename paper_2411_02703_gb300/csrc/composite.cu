@@ -363,20 +363,31 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
         const int lp = bp.lp0 + j * TW;
         float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
         int last = 0, stop = -1;
+        // the six fields of chunk k + 1 are loaded while chunk k is combined
+        float f[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) f[q] = slot_field(cp, s0, q, TPX)[lp];
         for (uint32_t k = 0; k < nch; ++k) {
-            const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
-            const int lk = __float_as_int(slot_field(cp, s0 + k, 5, TPX)[lp]);
+            float g[6];
+            if (k + 1 < nch) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) g[q] = slot_field(cp, s0 + k + 1, q, TPX)[lp];
+            }
+            const float Tk = f[4];
+            const int lk = __float_as_int(f[5]);
             const float Tn = __fmul_rn(T, Tk);
             if ((lk & (int)0x80000000) || Tn < kTMin) {
                 stop = (int)k;
                 break;
             }
-            C0 = fmaf(T, slot_field(cp, s0 + k, 0, TPX)[lp], C0);
-            C1 = fmaf(T, slot_field(cp, s0 + k, 1, TPX)[lp], C1);
-            C2 = fmaf(T, slot_field(cp, s0 + k, 2, TPX)[lp], C2);
-            D = fmaf(T, slot_field(cp, s0 + k, 3, TPX)[lp], D);
+            C0 = fmaf(T, f[0], C0);
+            C1 = fmaf(T, f[1], C1);
+            C2 = fmaf(T, f[2], C2);
+            D = fmaf(T, f[3], D);
             T = Tn;
             if (lk) last = lk;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) f[q] = g[q];
         }
         const size_t gp = V.pix_base + (size_t)py * V.W + bp.px;
         PixState st{stop, 0, T, C0, C1, C2, D, T, C0, C1, C2, D, last, 0};
@@ -532,27 +543,51 @@ combine_state_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp, const PixSta
         const uint32_t top = stop >= 0 ? (uint32_t)stop : nch - 1;
         // each slot before the stop chunk becomes (its contribution, T at its end);
         // the stop chunk's slot was written by the exact walk
+        // (both loops load the next chunk's fields while handling the current one)
         float t = 1.f;
-        for (uint32_t k = 0; k < top || (stop < 0 && k == top); ++k) {
-            const float Tk = slot_field(cp, s0 + k, 4, TPX)[lp];
-            const float tend = __fmul_rn(t, Tk);
+        const uint32_t n_fwd = stop < 0 ? top + 1 : top;
+        {
+            float h[5];
+            if (n_fwd > 0) {
 #pragma unroll
-            for (int f = 0; f < 4; ++f) slot_field(cp, s0 + k, f, TPX)[lp] *= t;
-            slot_field(cp, s0 + k, 4, TPX)[lp] = t - tend;
-            slot_field(cp, s0 + k, 5, TPX)[lp] = tend;
-            t = tend;
+                for (int q = 0; q < 5; ++q) h[q] = slot_field(cp, s0, q, TPX)[lp];
+            }
+            for (uint32_t k = 0; k < n_fwd; ++k) {
+                float nx[5];
+                if (k + 1 < n_fwd) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) nx[q] = slot_field(cp, s0 + k + 1, q, TPX)[lp];
+                }
+                const float tend = __fmul_rn(t, h[4]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) slot_field(cp, s0 + k, q, TPX)[lp] = h[q] * t;
+                slot_field(cp, s0 + k, 4, TPX)[lp] = t - tend;
+                slot_field(cp, s0 + k, 5, TPX)[lp] = tend;
+                t = tend;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) h[q] = nx[q];
+            }
         }
         float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int k = (int)top; k >= 0; --k) {
-            float g[5];
+        {
+            float h[6];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) g[f] = slot_field(cp, s0 + k, f, TPX)[lp];
-            const float tend = slot_field(cp, s0 + k, 5, TPX)[lp];
-            const float inv = tend > 0.f ? 1.f / tend : 0.f;
+            for (int q = 0; q < 6; ++q) h[q] = slot_field(cp, s0 + top, q, TPX)[lp];
+            for (int k = (int)top; k >= 0; --k) {
+                float nx[6];
+                if (k > 0) {
 #pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                slot_field(cp, s0 + k, f, TPX)[lp] = acc[f] * inv;
-                acc[f] += g[f];
+                    for (int q = 0; q < 6; ++q) nx[q] = slot_field(cp, s0 + k - 1, q, TPX)[lp];
+                }
+                const float tend = h[5];
+                const float inv = tend > 0.f ? 1.f / tend : 0.f;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    slot_field(cp, s0 + k, q, TPX)[lp] = acc[q] * inv;
+                    acc[q] += h[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) h[q] = nx[q];
             }
         }
     }
