@@ -52,6 +52,26 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def reduce_max(x, dist=None):
+    """Maximum of x over the ranks of the default process group (x itself
+    without one); the tensor lives on the GPU for NCCL and on the host
+    otherwise."""
+    if dist is None:
+        return x
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, ms_per_step_max):
+    """Whole-job steps/s of `world` replicas, each timing its own steps: every
+    rank completes one step per max-over-ranks step time."""
+    return world * 1000.0 / ms_per_step_max
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -211,11 +231,7 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist)
 
     def step():
         lv.train_step_batched(dev, cams, levels, gts, lis, lam, lamd, grads=grads)
@@ -334,7 +350,7 @@ def run_ours(args):
                 "frac": ach / hbm_peak, "traffic": recorded_traffic(dominant), "peak_source": peak_kind}
 
     steps_per_s = 1000.0 / ms_batched
-    value = world * steps_per_s
+    value = job_throughput(world, ms_batched)
     out = {
         "metric": METRIC,
         "value": round(value, 4),
