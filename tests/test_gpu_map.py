@@ -336,3 +336,33 @@ def test_mapper_reduces_loss(pkg, ctx):
     assert sum(kf.iters for kf in kfs) == 3 * 30 and steps >= 3 + 87 // 2
     assert all(a < 0.9 * b for a, b in zip(after, before))
     assert gm.sh_degree == 3
+
+
+def test_map_edge_cases(pkg, ctx):
+    """Empty appends, a filter that drops every point, pruning everything, and
+    an Adam step on an empty map."""
+    rng = np.random.default_rng(8)
+    pts = rng.normal(0, 1, (100, 3)).astype(np.float32) + np.array([0, 0, 6], np.float32)
+    col = rng.uniform(0, 1, (100, 3)).astype(np.float32)
+    gm = pkg.GaussianMap(capacity=8, sh_stride_k=4)
+    # nothing to add
+    assert gm.append(ctx, torch.zeros((0, 3), device="cuda"), torch.zeros((0, 3), device="cuda")) == 0
+    assert gm.n == 0
+    gm.adam_step()  # empty map: no work, no error
+    # a fully opaque keyframe drops every point in view; the rest (none) is kept
+    cam = S.CameraSpec(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 50.0, 50.0, 32.0, 24.0, 64, 48)
+    import oracle as O
+
+    _, _, inview = M.point_pixels(pts, O.Camera(cam.R, cam.t, cam.fx, cam.fy, cam.cx, cam.cy, cam.W, cam.H))
+    alpha = torch.ones((48, 64), device="cuda")
+    added = gm.append(ctx, torch.from_numpy(pts).cuda(), torch.from_numpy(col).cuda(), cam, 0, alpha)
+    assert added == int((~inview).sum())
+    n_keep = gm.n
+    # a transparent keyframe keeps everything (and grows the buffers)
+    added = gm.append(ctx, torch.from_numpy(pts).cuda(), torch.from_numpy(col).cuda(), cam, 0,
+                      torch.zeros((48, 64), device="cuda"))
+    assert added == 100 and gm.n == n_keep + 100 and gm.capacity >= gm.n
+    # opacity 0.1 everywhere: pruning at 0.5 removes all, at 0.05 none
+    assert gm.prune(ctx, 0.05) == 0
+    assert gm.prune(ctx, 0.5) == n_keep + 100 and gm.n == 0
+    gm.adam_step()
