@@ -135,13 +135,14 @@ def preprocess(params, cam: Camera, tile=(16, 16)):
     out = dict(z_f=np.zeros(n, np.float32), uv_f=np.zeros((n, 2), np.float32),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                tiles=np.zeros(n, np.uint32), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
-               opacity=np.zeros(n), rgb=np.zeros((n, 3)), depth=np.zeros(n))
+               opacity=np.zeros(n), rgb=np.zeros((n, 3)), depth=np.zeros(n), conic_f=np.zeros((n, 3)))
     c = cam._c()
     rc = _load().orc_preprocess(
         ctypes.c_int64(n), _p(means), _p(ls), _p(q), _p(ol), _p(sh), ctypes.c_int(K),
         ctypes.c_int(deg), ctypes.byref(c), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
         _p(out["z_f"]), _p(out["uv_f"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]),
-        _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]), _p(out["depth"]))
+        _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]), _p(out["depth"]),
+        _p(out["conic_f"]))
     if rc:
         raise ValueError(f"orc_preprocess failed ({rc})")
     out["tiles_x"] = (cam.W + tile[0] - 1) // tile[0]
@@ -173,7 +174,13 @@ def tile_ranges(keys, n_tiles: int, tile_base: int = 0):
 
 
 def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None):
-    """a5: binary64 compositing.  ``sel_tiles`` limits the work to some tiles."""
+    """a5: binary64 compositing.  ``sel_tiles`` limits the work to some tiles.
+
+    ``margin`` is, per pixel, the smallest relative distance of any of its
+    threshold tests to the threshold; when ``pre`` carries the key stage's
+    binary32 centre (``uv_f``) and covariance inverse (``conic_f``), the
+    distance of the alpha, o G and T tests is net of the deviation binary32
+    inputs and evaluation may cause (see orc_render)."""
     P = W * H
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), alpha=np.zeros((H, W)),
                final_T=np.ones((H, W)), n_contrib=np.zeros((H, W), np.int32),
@@ -181,6 +188,12 @@ def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None):
     sel = None if sel_tiles is None else np.ascontiguousarray(sel_tiles, np.int32)
     if sel is not None and sel.shape[0] == 0:
         return out
+    uv_f, conic_f = pre.get("uv_f"), pre.get("conic_f")
+    if uv_f is None or conic_f is None:
+        uv_f = conic_f = None
+    else:
+        uv_f = np.ascontiguousarray(uv_f, np.float32)
+        conic_f = np.ascontiguousarray(conic_f, np.float64)
     v = np.ascontiguousarray(vals, np.uint32)
     rg = np.ascontiguousarray(ranges, np.uint32)
     rc = _load().orc_render(
@@ -188,7 +201,8 @@ def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None):
         _p(pre["uv"]), _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]), _p(pre["depth"]),
         _p(v), _p(rg), ctypes.c_int(0 if sel is None else sel.shape[0]), _p(sel),
         _p(out["rgb"]), _p(out["depth"]), _p(out["alpha"]), _p(out["final_T"]),
-        _p(out["n_contrib"]), _p(out["margin"]), _p(out["signature"]))
+        _p(out["n_contrib"]), _p(out["margin"]), _p(out["signature"]),
+        _p(uv_f), _p(conic_f))
     if rc:
         raise ValueError(f"orc_render failed ({rc})")
     del P

@@ -147,6 +147,7 @@ typedef struct {
     int visible;         /* 0: culled (behind the near plane or singular)  */
     float z;             /* view-space depth, the low half of the key      */
     float u, v;          /* screen position                                */
+    float a, b, c, det;  /* dilated 2D covariance and its determinant      */
     int radius;          /* ceil(3 sqrt(lambda_max))                       */
     int x0, y0, x1, y1;  /* covered tile rectangle, [x0,x1) x [y0,y1)      */
 } key_stage_t;
@@ -240,6 +241,10 @@ static void key_stage(const float *m, const float *ls, const float *q, const orc
     o->z = pz;
     o->u = u;
     o->v = v;
+    o->a = a;
+    o->b = b;
+    o->c = cc;
+    o->det = det;
     o->radius = rad;
     o->x0 = (int)clamp_tile((u - fr) / (float)tw, tiles_x);
     o->x1 = (int)clamp_tile((u + fr + (float)(tw - 1)) / (float)tw, tiles_x);
@@ -349,12 +354,17 @@ static void value_stage(const float *m, const float *ls, const float *q, float o
 /* a1: preprocess one view.                                                  */
 /* Key outputs (float/int): z, u, v, radius, rect[4], tiles_touched.         */
 /* Value outputs (double):  uv[2], conic[3], opacity, rgb[3], depth.         */
+/* conic_f[3] (optional): the inverse of the key stage's binary32 covariance */
+/* (its binary32 a, b, c over its binary32 determinant), taken in binary64:  */
+/* the conic a binary32 compositing stage starts from, for the error         */
+/* allowance of the render margins.                                          */
 /* ------------------------------------------------------------------------ */
 int orc_preprocess(int64_t n, const float *means, const float *log_scales, const float *quats,
                    const float *opacity_logits, const float *sh, int sh_stride_k, int sh_degree,
                    const orc_camera *cam, int tile_w, int tile_h,
                    float *z_f, float *uv_f, int32_t *radius, int32_t *rect, uint32_t *tiles,
-                   double *uv, double *conic, double *opacity, double *rgb, double *depth) {
+                   double *uv, double *conic, double *opacity, double *rgb, double *depth,
+                   double *conic_f) {
     if (n < 0 || tile_w <= 0 || tile_h <= 0 || sh_degree < 0 || sh_degree > 3 ||
         sh_stride_k < (sh_degree + 1) * (sh_degree + 1))
         return ORC_ERR_ARG;
@@ -371,6 +381,15 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
         radius[i] = k.visible ? k.radius : 0;
         rect[4 * i] = k.x0; rect[4 * i + 1] = k.y0; rect[4 * i + 2] = k.x1; rect[4 * i + 3] = k.y1;
         tiles[i] = k.visible ? (uint32_t)((k.x1 - k.x0) * (k.y1 - k.y0)) : 0u;
+        if (conic_f) {
+            if (k.visible) {
+                conic_f[3 * i] = (double)k.c / (double)k.det;
+                conic_f[3 * i + 1] = -(double)k.b / (double)k.det;
+                conic_f[3 * i + 2] = (double)k.a / (double)k.det;
+            } else {
+                conic_f[3 * i] = conic_f[3 * i + 1] = conic_f[3 * i + 2] = 0;
+            }
+        }
         if (!k.visible) {
             uv[2 * i] = uv[2 * i + 1] = 0;
             conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0;
@@ -452,6 +471,17 @@ int orc_tile_ranges(int64_t m, const uint64_t *keys, uint32_t tile_base, int n_t
 /* sorted list.  Also reports the smallest relative distance of any test to  */
 /* its threshold, so callers can excuse pixels where binary32 arithmetic may */
 /* legitimately take the other branch.                                       */
+/*                                                                           */
+/* With uv_f / conic_f (the binary32 centre of the key stage and the conic   */
+/* of its binary32 covariance) the distance of each test on alpha, o G and T */
+/* is net of an allowance for binary32: the exponent moves by                */
+/*   d_in  = |power(uv_f, conic_f) - power(uv, conic)|                       */
+/* (the deviation the binary32 inputs force, evaluated in binary64) plus     */
+/*   d_ev  = 16 u (scale + 1),  u = 2^-24,                                   */
+/* for the rounding of evaluating it and of the exponential, and alpha and   */
+/* o G move by the same amount relatively (first order).  T's relative       */
+/* allowance grows by alpha / (1 - alpha) times that, plus 2 u, per blended  */
+/* Gaussian.  The power > 0 test keeps its plain distance |power| / scale.   */
 /* ------------------------------------------------------------------------ */
 #define ALPHA_MAX 0.99
 #define ALPHA_MIN (1.0 / 255.0)
@@ -459,11 +489,15 @@ int orc_tile_ranges(int64_t m, const uint64_t *keys, uint32_t tile_base, int n_t
 
 static double rel_margin(double x, double thr) { return fabs(x - thr) / fabs(thr); }
 
+#define U32 (1.0 / 16777216.0)
+
 int orc_render(int W, int H, int tile_w, int tile_h, const double *uv, const double *conic,
                const double *opacity, const double *rgb, const double *depth,
                const uint32_t *vals, const uint32_t *ranges, int n_sel, const int32_t *sel_tiles,
                double *out_rgb, double *out_depth, double *out_alpha, double *out_T,
-               int32_t *out_ncontrib, double *out_margin, uint64_t *out_sig) {
+               int32_t *out_ncontrib, double *out_margin, uint64_t *out_sig,
+               const float *uv_f, const double *conic_f) {
+    const int allow = uv_f && conic_f;
     int tiles_x = (W + tile_w - 1) / tile_w;
     int tiles_y = (H + tile_h - 1) / tile_h;
     int nt = sel_tiles ? n_sel : tiles_x * tiles_y;
@@ -476,6 +510,7 @@ int orc_render(int W, int H, int tile_w, int tile_h, const double *uv, const dou
         for (int py = ty * tile_h; py < (ty + 1) * tile_h && py < H; ++py)
             for (int px = tx * tile_w; px < (tx + 1) * tile_w && px < W; ++px) {
                 double T = 1.0, C[3] = {0, 0, 0}, D = 0, margin = INFINITY;
+                double eT = 0; /* relative allowance of T */
                 int32_t last = 0;
                 uint64_t sig = 1469598103934665603ull; /* FNV-1a of the contributing positions */
                 for (uint32_t j = s; j < e; ++j) {
@@ -485,16 +520,25 @@ int orc_render(int W, int H, int tile_w, int tile_h, const double *uv, const dou
                     double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
                     double scale = 0.5 * (fabs(A) * dx * dx + fabs(Cc) * dy * dy) + fabs(B * dx * dy);
                     if (scale > 0) { double mp = fabs(power) / scale; if (mp < margin) margin = mp; }
+                    double da = 0; /* relative allowance of o G and alpha */
+                    if (allow) {
+                        double fx = (double)uv_f[2 * g] - px, fy = (double)uv_f[2 * g + 1] - py;
+                        double Af = conic_f[3 * g], Bf = conic_f[3 * g + 1], Cf = conic_f[3 * g + 2];
+                        double pf = -0.5 * (Af * fx * fx + Cf * fy * fy) - Bf * fx * fy;
+                        double sf = 0.5 * (fabs(Af) * fx * fx + fabs(Cf) * fy * fy) + fabs(Bf * fx * fy);
+                        da = fabs(pf - power) + 16.0 * U32 * (sf + 1.0);
+                    }
                     if (power > 0) continue;
                     double oG = opacity[g] * exp(power);
-                    double mc = rel_margin(oG, ALPHA_MAX);
+                    double mc = rel_margin(oG, ALPHA_MAX) - da;
                     if (mc < margin) margin = mc;
                     double alpha = oG < ALPHA_MAX ? oG : ALPHA_MAX;
-                    double ma = rel_margin(alpha, ALPHA_MIN);
+                    double ma = rel_margin(alpha, ALPHA_MIN) - da;
                     if (ma < margin) margin = ma;
                     if (alpha < ALPHA_MIN) continue;
                     double Tn = T * (1.0 - alpha);
-                    double mt = rel_margin(Tn, T_MIN);
+                    if (allow) eT += alpha / (1.0 - alpha) * da + 2.0 * U32;
+                    double mt = rel_margin(Tn, T_MIN) - eT;
                     if (mt < margin) margin = mt;
                     if (Tn < T_MIN) break;
                     for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * alpha * T;

@@ -5,7 +5,11 @@ absolute; gradients within 1e-3 relative (with an absolute floor of 1e-3 of
 the tensor's largest entry).  Pixels where the oracle sees a threshold test
 (power vs 0, alpha vs 1/255, o*G vs 0.99, T vs 1e-4) within a relative
 margin of 1e-4 may take the other branch in binary32; they are excused and
-counted, and so are the gradients of Gaussians listed in their tiles.
+counted, and so are the gradients of Gaussians listed in their tiles.  The
+oracle's margin of the alpha, o*G and T tests is net of the deviation that the
+binary32 screen position and covariance (bit-exact on both sides) and the
+binary32 evaluation of the exponent may cause: a Gaussian one pixel wide at
+u = 600 moves its exponent by ~1e-4 from the rounding of u alone.
 """
 import functools
 import math
@@ -89,7 +93,14 @@ def grad_check(name, g, r, excl=None, rtol=GRAD_RTOL):
     bound = rtol * np.abs(r[mask]) + rtol * scale
     worst = (err / np.maximum(bound, 1e-30)).max(initial=0.0)
     rel_norm = np.linalg.norm(err) / max(np.linalg.norm(r[mask]), 1e-30)
-    print(f"  grad {name}: max err/bound {worst:.3f}  rel-norm err {rel_norm:.2e}  scale {scale:.3e}")
+    msg = f"  grad {name}: max err/bound {worst:.3f}  rel-norm err {rel_norm:.2e}  scale {scale:.3e}"
+    if not mask.all():
+        # the excused rows still count in the whole tensor's relative norm: a
+        # branch taken the other way moves a few pixels' terms, not the tensor
+        all_norm = np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-30)
+        msg += f"  (all rows: rel-norm err {all_norm:.2e})"
+        assert all_norm <= rtol, f"{name}: relative norm error {all_norm:.2e} over all rows"
+    print(msg)
     assert (err <= bound).all(), f"{name}: {int((err > bound).sum())} entries beyond tolerance"
 
 
@@ -460,3 +471,49 @@ def test_autotune_then_batched_matches_plain(pkg):
         rgb, depth, alpha, slot = plain.render(dp, c, l)
         plain.release(slot)
         assert torch.equal(rgb, outs[i][0]) and torch.equal(alpha, outs[i][2])
+
+
+def test_headline_step_full_size(pkg):
+    """The benchmarked step itself, against the oracle's full step: 1M Gaussians
+    (SH 3), 8 keyframes at levels [2,2,2,2,1,0,2,1], one graph-replayed batched
+    call (16x16 tiles).  Every pixel of every view, the four loss terms of every
+    view and every parameter gradient, with the threshold excusals of the other
+    chained-step tests (pixels within the 1e-4 margin, dilated by the SSIM
+    half-window, and the Gaussians listed in their tiles)."""
+    from scipy.ndimage import binary_dilation
+
+    margin = MARGIN
+
+    wl = S.workload("lidar_1000000_8v")
+    params, cams, levels = wl["params"], wl["cams"], wl["levels"]
+    lv = pkg.Context(tile=(16, 16))
+    dp = dev_params(params)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gts, lis = [t(x) for x in wl["gts"]], [t(x) for x in wl["lidars"]]
+    outs = [(torch.empty(3, c.H >> l, c.W >> l, device="cuda"), torch.empty(c.H >> l, c.W >> l, device="cuda"),
+             torch.empty(c.H >> l, c.W >> l, device="cuda")) for c, l in zip(cams, levels)]
+    for _ in range(3):  # eager sizing, capture, replay
+        losses, grads = lv.train_step_batched(dp, cams, levels, gts, lis, wl["lam"], wl["lam_d"], outputs=outs)
+    torch.cuda.synchronize()
+    lv.sync_status()
+    ocams = [ocam(c) for c in cams]
+    out, rgrads = O.train_step(params, ocams, levels, wl["gts"], wl["lidars"], wl["lam"], wl["lam_d"])
+    excl = set()
+    for i, (c, l) in enumerate(zip(cams, levels)):
+        r = out[i]["render"]
+        exc = r["margin"] <= margin
+        e = compare_images(outs[i], r, exc)
+        print(f"  view {i} level {l}: excused {exc.mean():.4%}, max err rgb {e[0]:.2e} depth {e[1]:.2e} "
+              f"alpha {e[2]:.2e}")
+        assert exc.mean() < 0.02
+        assert e[0] < IMG_TOL and e[2] < IMG_TOL
+        assert e[1] < IMG_TOL * max(1.0, float(np.abs(r["depth"]).max()))
+        np.testing.assert_allclose(losses[i].cpu().numpy(), out[i]["terms"], rtol=2e-4, atol=1e-7)
+        if exc.any():
+            exc = binary_dilation(exc, iterations=5)
+        excl.update(excused_tiles_gaussians(r, (16, 16), r["cam"].W, r["cam"].H, exc).tolist())
+    excl = np.array(sorted(excl), dtype=np.int64)
+    print(f"  Gaussians excused from the gradient bar: {len(excl)} of {params['means'].shape[0]}")
+    for k in pkg.PARAM_NAMES:
+        grad_check(k, grads[k].cpu().numpy(), rgrads[k], excl, rtol=2e-3)
+    lv.close()
