@@ -495,3 +495,64 @@ def test_exp_key_is_binary64_exp_rounded_once():
                         [0.0, -0.0, 1e-30, -1e-30, 59.9, -59.9, 88.0, -100.0]]).astype(np.float32)
     ref = np.exp(x.astype(np.float64)).astype(np.float32)
     np.testing.assert_array_equal(O.exp_key(x), ref)
+
+
+def test_render_margin_allowance_covers_binary32_evaluation():
+    """The render margin's binary32 allowance: (1) the conic of the binary32
+    covariance is the float64 conic up to binary32 rounding (amplified where
+    the projection cancels a 3D covariance elongated along the ray); (2) the allowance
+    only lowers margins; (3) an independent binary32 evaluation of every
+    examined alpha (numpy float32: the key stage's centre, that conic rounded to
+    binary32, float32 exp) takes the 1/255 and 0.99 decisions the other way
+    only at pixels whose margin is at most 0."""
+    params, phase = S.lidar_scene(300_000)
+    cam = O.level_camera(cam_of(S.trajectory_cameras(1, phase=phase)[0]), 1)
+    pre = O.preprocess(params, cam)
+    vis = pre["radius"] > 0
+    cf, c64 = pre["conic_f"][vis], pre["conic"][vis]
+    dev = np.abs(cf - c64).max(axis=1) / np.abs(c64).max(axis=1)
+    assert np.median(dev) < 1e-6 and dev.max() < 1e-4
+
+    keys, vals = O.build_keys(pre)
+    ranges = O.tile_ranges(keys, pre["tiles_x"] * pre["tiles_y"])
+    sel = np.random.default_rng(5).choice(ranges.shape[0], 160, replace=False).astype(np.int32)
+    img = O.render(pre, vals, ranges, cam.W, cam.H, sel_tiles=sel)
+    plain = dict(pre)
+    del plain["conic_f"]
+    img0 = O.render(plain, vals, ranges, cam.W, cam.H, sel_tiles=sel)
+    assert np.all(img["margin"] <= img0["margin"])
+    assert np.array_equal(img["rgb"], img0["rgb"]) and np.array_equal(img["n_contrib"], img0["n_contrib"])
+
+    f = np.float32
+    uvf = pre["uv_f"]
+    cf32 = pre["conic_f"].astype(f)
+    op32 = pre["opacity"].astype(f)
+    flips = plain_beyond = 0
+    tx_n = pre["tiles_x"]
+    for t in sel:
+        s, e = (int(x) for x in ranges[t])
+        if e <= s:
+            continue
+        g = vals[s:e]
+        ty, tx = divmod(t, tx_n)
+        ys, xs = np.mgrid[ty * 16:min(ty * 16 + 16, cam.H), tx * 16:min(tx * 16 + 16, cam.W)]
+        ys, xs = ys.ravel(), xs.ravel()
+        dx64 = pre["uv"][g, 0][None] - xs[:, None]
+        dy64 = pre["uv"][g, 1][None] - ys[:, None]
+        A, B, C = (pre["conic"][g, k][None] for k in range(3))
+        p64 = -0.5 * (A * dx64 * dx64 + C * dy64 * dy64) - B * dx64 * dy64
+        a64 = pre["opacity"][g][None] * np.exp(p64)
+        dx = uvf[g, 0][None] - xs[:, None].astype(f)
+        dy = uvf[g, 1][None] - ys[:, None].astype(f)
+        A32, B32, C32 = (cf32[g, k][None] for k in range(3))
+        p32 = f(-0.5) * (A32 * dx * dx + C32 * dy * dy) - B32 * dx * dy
+        a32 = op32[g][None] * np.exp(p32)
+        examined = np.arange(e - s)[None] < img["n_contrib"][ys, xs][:, None]
+        flip = examined & (p64 <= 0) & (((a64 >= 1 / 255) != (a32 >= f(1 / 255))) | ((a64 >= 0.99) != (a32 >= f(0.99))))
+        rows = np.nonzero(flip.any(axis=1))[0]
+        flips += rows.size
+        plain_beyond += int((img0["margin"][ys[rows], xs[rows]] > 0.0).sum())
+        assert np.all(img["margin"][ys[rows], xs[rows]] <= 0.0)
+    print(f"  binary32 decision flips at {flips} pixels, all within the allowance "
+          f"({plain_beyond} beyond the plain margin)")
+    assert flips > 0
