@@ -58,10 +58,38 @@ constexpr int kWarpsPerCta = 4;
 constexpr int kFields = 6; // per (pixel, chunk) slot and checkpoint
 constexpr int kSub = 8;    // checkpoint groups per chunk: after each eighth (the last is the chunk's end)
 
-// does the alpha box of record (a, b, c) meet the block [x0, x0+7] x [y0, y0+7]?
+// Can record (a, b, c) reach alpha >= 1/255 anywhere in the block
+// [x0, x0+7] x [y0, y0+7]?  First the conservative box of that region
+// (half-extents from preprocessing), then the ellipse itself: the largest
+// base-2 exponent e2 = a2 dx^2 + b2 dx dy + c2 dy^2 over the block (concave,
+// so either 0 at the centre or on one of the four edges, where the best
+// offset along the edge is a clamped closed form) against log2(1/(255 o)).
+// The comparison keeps a slack of 0.05 plus 2e-6 of the largest term any
+// pixel of the block can have, far above the rounding of both this bound
+// and the per-pixel exponent, so a culled Gaussian fails the 1/255 test at
+// every pixel of the block.
 __device__ __forceinline__ bool meets(const float4 a, const float4 b, const float4 c, float x0, float y0) {
     const float ex = b.w, ey = c.w;
-    return a.x + ex >= x0 && a.x - ex <= x0 + (PB - 1) && a.y + ey >= y0 && a.y - ey <= y0 + (PB - 1);
+    if (!(a.x + ex >= x0 && a.x - ex <= x0 + (PB - 1) && a.y + ey >= y0 && a.y - ey <= y0 + (PB - 1)))
+        return false;
+    // dx = u - px over [X0, X1], dy = v - py over [Y0, Y1]
+    const float X1 = a.x - x0, X0 = X1 - (float)(PB - 1);
+    const float Y1 = a.y - y0, Y0 = Y1 - (float)(PB - 1);
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+    const float a2 = a.z, b2 = a.w, c2 = b.x; // a2, c2 < 0
+    const float ka = __fdividef(-0.5f * b2, a2), kc = __fdividef(-0.5f * b2, c2);
+    float best = -INFINITY;
+    {
+        const float dx0 = fminf(fmaxf(ka * Y0, X0), X1), dx1 = fminf(fmaxf(ka * Y1, X0), X1);
+        best = fmaxf(best, fmaf(dx0, fmaf(a2, dx0, b2 * Y0), c2 * Y0 * Y0));
+        best = fmaxf(best, fmaf(dx1, fmaf(a2, dx1, b2 * Y1), c2 * Y1 * Y1));
+        const float dy0 = fminf(fmaxf(kc * X0, Y0), Y1), dy1 = fminf(fmaxf(kc * X1, Y0), Y1);
+        best = fmaxf(best, fmaf(dy0, fmaf(c2, dy0, b2 * X0), a2 * X0 * X0));
+        best = fmaxf(best, fmaf(dy1, fmaf(c2, dy1, b2 * X1), a2 * X1 * X1));
+    }
+    const float mx = fmaxf(fabsf(X0), fabsf(X1)), my = fmaxf(fabsf(Y0), fabsf(Y1));
+    const float big = fmaf(-a2, mx * mx, fmaf(fabsf(b2), mx * my, -c2 * my * my));
+    return best + fmaf(2e-6f, big, 0.05f) >= -__log2f(255.f * b.y);
 }
 
 template <int TW, int TH>
