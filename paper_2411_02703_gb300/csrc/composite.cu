@@ -194,6 +194,12 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             g[5 * ck.tpx + lp] = __int_as_float(last[k] | (stopped[k] ? (int)0x80000000 : 0));
         }
     };
+    // Without START a finished pixel is skipped by raising its alpha threshold
+    // above any alpha (one test instead of two per evaluation); the re-walk
+    // with START keeps the separate test, which its register budget prefers.
+    float thr[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) thr[k] = (!START && done[k]) ? 2.f : kAlphaMin;
     for (uint32_t base = lo; base < hi; base += B) {
         if (__all_sync(0xffffffffu, tdone)) {
             // every pixel is finished: the remaining checkpoints hold the final state
@@ -210,17 +216,18 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             if (START) qpos = sm.Pos[q];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (done[k]) continue;
-                if (START && qpos < start[k]) continue;
+                if (START && (done[k] || qpos < start[k])) continue;
                 const float dy = a.y - (float)(py0 + k);
+                // no test of e2 > 0: the conic is positive definite, so a
+                // positive exponent is rounding at the centre, where alpha is o
                 const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy);
-                if (e2 > 0.f) continue;
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, exp2_approx(e2)));
-                if (alpha < kAlphaMin) continue;
+                if (alpha < (START ? kAlphaMin : thr[k])) continue;
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
                     done[k] = true;
                     stopped[k] = true;
+                    thr[k] = 2.f;
                     continue;
                 }
                 const float4 c = sm.C[q];
@@ -755,8 +762,7 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 for (int j = 0; j < PPT; ++j) {
                     if (pos >= last[j]) continue;
                     const float dy = a.y - (float)(bp.py0 + j);
-                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy);
-                    if (e2 > 0.f) continue;
+                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy); // no e2 > 0 test, as forward
                     const float G_ = exp2_approx(e2);
                     const float oG = __fmul_rn(b.y, G_);
                     const float alpha = fminf(kAlphaMax, oG);

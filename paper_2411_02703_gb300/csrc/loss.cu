@@ -123,22 +123,28 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
     const int px = tx * LT + vc;
     const float lam = lv.lambda_ssim;
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    double l1 = 0.0, ssim = 0.0, dsum = 0.0, dcnt = 0.0;
+    // a thread's own sums (at most 12 terms each) in binary32, the block's in binary64
+    float l1 = 0.f, ssim = 0.f, dsum = 0.f, dcnt = 0.f;
     float *G = gmaps + lv.gmap_base[vi];
 
     for (int ch = 0; ch < 3; ++ch) {
         const float *x = lv.rgb[vi] + ch * HW;
         const float *y = lv.gt[vi] + ch * HW;
+        if (lam == 0.f) {
 #pragma unroll
-        for (int o = 0; o < RUN; ++o) {
-            const int py = ty * LT + vr + o;
-            if (px < W && py < H) l1 += fabsf(x[(size_t)py * W + px] - y[(size_t)py * W + px]);
+            for (int o = 0; o < RUN; ++o) {
+                const int py = ty * LT + vr + o;
+                if (px < W && py < H) l1 += fabsf(x[(size_t)py * W + px] - y[(size_t)py * W + px]);
+            }
+            continue;
         }
-        if (lam == 0.f) continue;
         __syncthreads();
         stage(x, W, H, tx, ty, sx);
         stage(y, W, H, tx, ty, sy);
         __syncthreads();
+        // L1 from the staged samples (zero outside the image on both sides)
+#pragma unroll
+        for (int o = 0; o < RUN; ++o) l1 += fabsf(sx[HALO + vr + o][HALO + vc] - sy[HALO + vr + o][HALO + vc]);
         // horizontal pass: runs of four outputs along the staged rows
         for (int task = t; task < kRowTasks; task += kThreads) {
             const int r = task / (LT / RUN), c0 = (task % (LT / RUN)) * RUN;
@@ -198,12 +204,13 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
             const float vx = mxx - mx * mx, vy = myy - my * my, cxy = mxy - mx * my;
             const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
             const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
-            const float inv = 1.f / (B1 * B2);
+            const float rB1 = __frcp_rn(B1), rB2 = __frcp_rn(B2);
+            const float inv = rB1 * rB2;
             const float S = A1 * A2 * inv;
             ssim += S;
             // dS/d mu_x, dS/d E[x^2], dS/d E[xy]
-            const float d1 = 2.f * my * (A2 - A1) * inv - S * (2.f * mx / B1 - 2.f * mx / B2);
-            const float d2 = -S / B2;
+            const float d1 = 2.f * my * (A2 - A1) * inv - S * (2.f * mx) * (rB1 - rB2);
+            const float d2 = -S * rB2;
             const float d12 = 2.f * A1 * inv;
             G[(0 * 3 + ch) * HW + p] = d1;
             G[(1 * 3 + ch) * HW + p] = d2;
@@ -219,7 +226,7 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
             const float L = lv.lidar[vi][p];
             if (L > 0.f) {
                 dsum += fabsf(lv.depth[vi][p] - L);
-                dcnt += 1.0;
+                dcnt += 1.f;
             }
         }
     }
@@ -347,16 +354,17 @@ loss_pass2_kernel(LossViews lv, Window win, const float *__restrict__ gmaps,
         }
     }
     if (lv.d_depth[vi]) {
+        const double nv = lv.lidar[vi] ? nvalid[vi] : 0.0;
+        const float gs = nv > 0 ? lv.lambda_depth / (float)nv : 0.f; // times a sign: exact
 #pragma unroll
         for (int o = 0; o < RUN; ++o) {
             const int py = ty * LT + vr + o;
             if (!(px < W && py < H)) continue;
             const size_t p = (size_t)py * W + px;
             float g = 0.f;
-            if (lv.lidar[vi]) {
+            if (gs != 0.f) {
                 const float L = lv.lidar[vi][p];
-                const double nv = nvalid[vi];
-                if (L > 0.f && nv > 0) g = lv.lambda_depth * sgnf(lv.depth[vi][p] - L) / (float)nv;
+                if (L > 0.f) g = gs * sgnf(lv.depth[vi][p] - L);
             }
             lv.d_depth[vi][p] = g;
         }
