@@ -153,15 +153,23 @@ radix_upsweep_kernel(const uint32_t *keys, const uint32_t *n_dev, uint32_t n_hos
     uint32_t begin, end;
     rs_chunk(n, G, blockIdx.x, begin, end);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // kRsItems keys per lane and round, all loaded before the first is counted;
-    // within an instruction the leaders of a digit's peers hit distinct bins
-    for (uint32_t i0 = begin + warp * (32 * kRsItems); i0 < end; i0 += kRsThreads * kRsItems) {
-        uint32_t d[kRsItems];
+    // kRsItems keys per lane and round, all loaded before the first is counted
+    // and the next round's loaded while this one is counted; within an
+    // instruction the leaders of a digit's peers hit distinct bins
+    uint32_t kn[kRsItems];
+    auto load = [&](uint32_t i0) {
 #pragma unroll
         for (int j = 0; j < kRsItems; ++j) {
             const uint32_t i = i0 + j * 32 + lane;
-            d[j] = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
+            kn[j] = i < end ? __ldg(keys + i) : 0u;
         }
+    };
+    load(begin + warp * (32 * kRsItems));
+    for (uint32_t i0 = begin + warp * (32 * kRsItems); i0 < end; i0 += kRsThreads * kRsItems) {
+        uint32_t d[kRsItems];
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) d[j] = i0 + j * 32 + lane < end ? (kn[j] >> shift) & 255u : 256u;
+        if (i0 + kRsThreads * kRsItems < end) load(i0 + kRsThreads * kRsItems);
 #pragma unroll
         for (int j = 0; j < kRsItems; ++j) {
             const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
@@ -207,7 +215,7 @@ radix_rowscan_kernel(uint32_t *counts, int G, uint32_t *totals) {
     if (t < G) counts[(size_t)d * G + t] = warp_sums[warp] + inc - x;
 }
 
-__global__ void __launch_bounds__(kRsThreads)
+__global__ void __launch_bounds__(kRsThreads, 3)
 radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                        uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                        const uint32_t *n_dev, uint32_t n_host, int shift, int G, const uint32_t *counts,
@@ -227,19 +235,30 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
     uint32_t begin, end;
     rs_chunk(n, G, blockIdx.x, begin, end);
     const uint32_t lt = lanemask_lt();
+    // the next tile's keys and values are loaded while this one is ranked
+    uint32_t kn[kRsItems], vn[kRsItems];
+    auto load = [&](uint32_t tile0) {
+#pragma unroll
+        for (int j = 0; j < kRsItems; ++j) {
+            const uint32_t i = tile0 + warp * (kRsItems * 32) + j * 32 + lane;
+            kn[j] = i < end ? keys_in[i] : 0u;
+            vn[j] = i < end ? vals_in[i] : 0u;
+        }
+    };
+    if (begin < end) load(begin);
     for (uint32_t tile0 = begin; tile0 < end; tile0 += kRsTile) {
 #pragma unroll
         for (int w = 0; w < kRsWarps; ++w) s_hist[w][t] = 0;
-        __syncthreads();
         uint32_t k[kRsItems], v[kRsItems], rank[kRsItems], d[kRsItems];
 #pragma unroll
         for (int j = 0; j < kRsItems; ++j) {
             const uint32_t i = tile0 + warp * (kRsItems * 32) + j * 32 + lane;
-            const bool valid = i < end;
-            k[j] = valid ? keys_in[i] : 0u;
-            v[j] = valid ? vals_in[i] : 0u;
-            d[j] = valid ? (k[j] >> shift) & 255u : 256u;
+            k[j] = kn[j];
+            v[j] = vn[j];
+            d[j] = i < end ? (k[j] >> shift) & 255u : 256u;
         }
+        if (tile0 + kRsTile < end) load(tile0 + kRsTile);
+        __syncthreads();
 #pragma unroll
         for (int j = 0; j < kRsItems; ++j) {
             const uint32_t peers = __match_any_sync(0xffffffffu, d[j]);
