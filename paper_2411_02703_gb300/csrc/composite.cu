@@ -40,7 +40,7 @@
 // Gaussian, so one running scalar per pixel replaces those five sums.  Each
 // lane sums over its two pixels ten terms: five moments of dL/dpower (times
 // dx, dy, dx^2, dx dy, dy^2; the conic enters once per Gaussian, in the
-// backward preprocess), dL/dopacity, and the colour and depth weights.  The
+// backward preprocess), o dL/dopacity, and the colour and depth weights.  The
 // warp reduce-scatters the ten sums with 12 shuffles, and the ten lanes that
 // end with a total add it to the Gaussian's gradient record with one atomic
 // instruction.
@@ -50,7 +50,6 @@ namespace lvigs {
 namespace {
 
 constexpr float kAlphaMax = 0.99f;
-constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;
 constexpr int PB = 8;  // warp pixel block is PB x PB
 constexpr int PPT = 2; // pixels per lane (rows 2r, 2r+1 of the block)
@@ -63,7 +62,8 @@ constexpr int kSub = 8;    // checkpoint groups per chunk: after each eighth (th
 // (half-extents from preprocessing), then the ellipse itself: the largest
 // base-2 exponent e2 = a2 dx^2 + b2 dx dy + c2 dy^2 over the block (concave,
 // so either 0 at the centre or on one of the four edges, where the best
-// offset along the edge is a clamped closed form) against log2(1/(255 o)).
+// offset along the edge is a clamped closed form) plus log2(o) against
+// log2(1/255).
 // The comparison keeps a slack of 0.05 plus 2e-6 of the largest term any
 // pixel of the block can have, far above the rounding of both this bound
 // and the per-pixel exponent, so a culled Gaussian fails the 1/255 test at
@@ -89,7 +89,7 @@ __device__ __forceinline__ bool meets(const float4 a, const float4 b, const floa
     }
     const float mx = fmaxf(fabsf(X0), fabsf(X1)), my = fmaxf(fabsf(Y0), fabsf(Y1));
     const float big = fmaf(-a2, mx * mx, fmaf(fabsf(b2), mx * my, -c2 * my * my));
-    return best + fmaf(2e-6f, big, 0.05f) >= -__log2f(255.f * b.y);
+    return best + b.y + fmaf(2e-6f, big, 0.05f) >= kLog2AlphaMin; // b.y = log2(o)
 }
 
 template <int TW, int TH>
@@ -199,7 +199,7 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
     // with START keeps the separate test, which its register budget prefers.
     float thr[PPT];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) thr[k] = (!START && done[k]) ? 2.f : kAlphaMin;
+    for (int k = 0; k < PPT; ++k) thr[k] = (!START && done[k]) ? 1e30f : kLog2AlphaMin;
     for (uint32_t base = lo; base < hi; base += B) {
         if (__all_sync(0xffffffffu, tdone)) {
             // every pixel is finished: the remaining checkpoints hold the final state
@@ -218,16 +218,16 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             for (int k = 0; k < PPT; ++k) {
                 if (START && (done[k] || qpos < start[k])) continue;
                 const float dy = a.y - (float)(py0 + k);
-                // no test of e2 > 0: the conic is positive definite, so a
-                // positive exponent is rounding at the centre, where alpha is o
-                const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy);
-                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, exp2_approx(e2)));
-                if (alpha < (START ? kAlphaMin : thr[k])) continue;
+                // e2 = log2(o G); no test of a positive power: the conic is
+                // positive definite, so one is rounding at the centre
+                const float e2 = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy);
+                if (e2 < (START ? kLog2AlphaMin : thr[k])) continue; // alpha < 1/255, or finished
+                const float alpha = fminf(kAlphaMax, exp2_approx(e2));
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
                     done[k] = true;
                     stopped[k] = true;
-                    thr[k] = 2.f;
+                    thr[k] = 1e30f;
                     continue;
                 }
                 const float4 c = sm.C[q];
@@ -752,7 +752,7 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 const float dx = a.x - fpx;
                 const float a2dx = __fmul_rn(a.z, dx);
                 // v: sums over the lane's pixels of dp dx, dp dy, dp dx^2, dp dx dy,
-                // dp dy^2 (dp = dL/dpower), dL/do, and w g_R, w g_G, w g_B, w g_D;
+                // dp dy^2 (dp = dL/dpower), o dL/do, and w g_R, w g_G, w g_B, w g_D;
                 // the conic is applied per Gaussian in the chain rule that follows
                 float v[NACC];
 #pragma unroll
@@ -762,11 +762,10 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                 for (int j = 0; j < PPT; ++j) {
                     if (pos >= last[j]) continue;
                     const float dy = a.y - (float)(bp.py0 + j);
-                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, dx, dy); // no e2 > 0 test, as forward
-                    const float G_ = exp2_approx(e2);
-                    const float oG = __fmul_rn(b.y, G_);
+                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy); // log2(o G), as forward
+                    if (e2 < kLog2AlphaMin) continue;
+                    const float oG = exp2_approx(e2);
                     const float alpha = fminf(kAlphaMax, oG);
-                    if (alpha < kAlphaMin) continue;
                     any = true;
                     T[j] = __fdividef(T[j], 1.f - alpha);
                     const float wgt = alpha * T[j];
@@ -780,7 +779,7 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                     if (oG < kAlphaMax) {
                         const float dp = dLda * alpha;
                         const float dpx = dp * dx, dpy = dp * dy;
-                        v[5] = fmaf(dLda, G_, v[5]);
+                        v[5] = fmaf(dLda, oG, v[5]); // o dL/do
                         v[0] += dpx;
                         v[1] += dpy;
                         v[2] = fmaf(dpx, dx, v[2]);

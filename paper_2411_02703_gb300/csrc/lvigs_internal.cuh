@@ -61,13 +61,14 @@ struct ParamGrads {
 };
 
 // Screen-space record of one (view, Gaussian), written by preprocessing and
-// gathered by the compositing kernels: a = (u, v, a2, b2), b = (c2, opacity, z,
-// ex), c = (r, g, b, ey).  With the conic [[A, B], [B, C]], the Gaussian's
-// exponent at offset (dx, dy) = (u - px, v - py) is power = -(A dx^2 + C dy^2)/2
+// gathered by the compositing kernels: a = (u, v, a2, b2), b = (c2, lo, z, ex),
+// c = (r, g, b, ey).  With the conic [[A, B], [B, C]], the Gaussian's exponent
+// at offset (dx, dy) = (u - px, v - py) is power = -(A dx^2 + C dy^2)/2
 // - B dx dy; the record holds it in base 2, a2 = -A log2(e) / 2,
-// b2 = -B log2(e), c2 = -C log2(e) / 2, so that exp(power) = 2^(a2 dx^2 +
-// b2 dx dy + c2 dy^2).  (ex, ey) are the half-extents of a box that holds
-// every pixel where alpha can reach 1/255.
+// b2 = -B log2(e), c2 = -C log2(e) / 2, together with lo = log2(opacity), so
+// that o exp(power) = 2^(a2 dx^2 + b2 dx dy + c2 dy^2 + lo): the 1/255 test is
+// a test of that exponent, taken before the exponential.  (ex, ey) are the
+// half-extents of a box that holds every pixel where alpha can reach 1/255.
 struct __align__(16) GRec {
     float4 a, b, c;
 };
@@ -94,12 +95,16 @@ __host__ __device__ inline int view_of_tile(const ViewSet &vs, uint32_t gt) {
 // Alpha of Eq. (6) at pixel offset (dx, dy) = (u - px, v - py).  Written with
 // explicit rounding so the forward and backward kernels take identical
 // branches on the 0.99 / (1/255) tests.
-// log2(e) * power at offset (dx, dy) from the record's coefficients, given
-// a2dx = a2 * dx (shared by the pixels of a column): dx (a2 dx + b2 dy) +
-// (c2 dy) dy, explicitly rounded so every kernel gets the same bits.
-__device__ __forceinline__ float gauss_exponent2(float a2dx, float b2, float c2, float dx, float dy) {
-    return __fmaf_rn(dx, __fmaf_rn(b2, dy, a2dx), __fmul_rn(__fmul_rn(c2, dy), dy));
+// log2(o exp(power)) at offset (dx, dy) from the record's coefficients,
+// given a2dx = a2 * dx (shared by the pixels of a column) and lo = log2(o):
+// dx (a2 dx + b2 dy) + ((c2 dy) dy + lo), explicitly rounded so every kernel
+// gets the same bits.
+__device__ __forceinline__ float gauss_exponent2(float a2dx, float b2, float c2, float lo, float dx, float dy) {
+    return __fmaf_rn(dx, __fmaf_rn(b2, dy, a2dx), __fmaf_rn(__fmul_rn(c2, dy), dy, lo));
 }
+
+// log2(1/255): alpha = min(0.99, 2^e) reaches 1/255 exactly when e >= this
+constexpr float kLog2AlphaMin = -7.99435343685885793770f;
 
 // 2^x by the hardware approximation (relative error about 2^-22).
 __device__ __forceinline__ float exp2_approx(float x) {

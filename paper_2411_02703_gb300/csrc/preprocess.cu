@@ -481,7 +481,7 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
         constexpr float kLog2e = 1.4426950408889634f;
         GRec rec;
         rec.a = make_float4(u, v, (c * inv_det) * (-0.5f * kLog2e), (b * inv_det) * kLog2e);
-        rec.b = make_float4((a * inv_det) * (-0.5f * kLog2e), op, pz, ex);
+        rec.b = make_float4((a * inv_det) * (-0.5f * kLog2e), log2f(op), pz, ex);
         rec.c = make_float4(rgb[0], rgb[1], rgb[2], ey);
         recs[o] = rec;
     }
@@ -786,7 +786,8 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
         const float qn[4] = {qw, qx, qy, qz};
         const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
-        const float d_logit = d_op * o * (1.f - o);
+        // the compositing backward accumulates o dL/do (its exponent holds log2 o)
+        const float d_logit = d_op * (1.f - o);
         if (!G.accumulate) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
