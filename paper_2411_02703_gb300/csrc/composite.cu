@@ -206,6 +206,18 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             for (; next_ck < n_ck; ++next_ck) store_ck(next_ck);
             break;
         }
+        if (START) {
+            // skip the batches before the earliest position an unfinished pixel
+            // still needs (pixels that resume further on leave gaps)
+            int need = 0x7fffffff;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (!done[k]) need = min(need, start[k]);
+            need = __reduce_min_sync(0xffffffffu, need);
+            const uint32_t at = rg_x + (uint32_t)need;
+            if (at >= base + B) base = lo + (at - lo) / B * B;
+            if (base >= hi) break;
+        }
         const int n = gather_cull<BM, false>(inst_vals, recs, rg_x, base, hi, fx0, fy0, sm, lane);
         for (int q = 0; q < n && !tdone; ++q) {
             const float4 a = sm.A[q];
@@ -391,67 +403,94 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
     const int vi = view_of_tile(*vsp, gt);
     const ViewDesc &V = vsp->v[vi];
     const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+    // the lane's two pixels are combined together (twice the loads in flight);
+    // the six fields of chunk k + 1 are loaded while chunk k is combined
+    bool act[PPT];
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], f[PPT][6];
+    int last[PPT], stop[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        act[j] = bp.px < V.W && bp.py0 + j < V.H;
+        T[j] = 1.f;
+        C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+        last[j] = 0;
+        stop[j] = -1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) f[j][q] = act[j] ? slot_field(cp, s0, q, TPX)[bp.lp0 + j * TW] : 0.f;
+    }
+    for (uint32_t k = 0; k < nch && (act[0] || act[1]); ++k) {
+        float g[PPT][6];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                g[j][q] = (act[j] && k + 1 < nch) ? slot_field(cp, s0 + k + 1, q, TPX)[bp.lp0 + j * TW] : 0.f;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            if (!act[j]) continue;
+            const float Tk = f[j][4];
+            const int lk = __float_as_int(f[j][5]);
+            const float Tn = __fmul_rn(T[j], Tk);
+            if ((lk & (int)0x80000000) || Tn < kTMin) {
+                stop[j] = (int)k;
+                act[j] = false;
+                continue;
+            }
+            C0[j] = fmaf(T[j], f[j][0], C0[j]);
+            C1[j] = fmaf(T[j], f[j][1], C1[j]);
+            C2[j] = fmaf(T[j], f[j][2], C2[j]);
+            D[j] = fmaf(T[j], f[j][3], D[j]);
+            T[j] = Tn;
+            if (lk) last[j] = lk;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) f[j][q] = g[j][q];
+        }
+    }
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         const int py = bp.py0 + j;
         if (!(bp.px < V.W && py < V.H)) continue;
         const int lp = bp.lp0 + j * TW;
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-        int last = 0, stop = -1;
-        // the six fields of chunk k + 1 are loaded while chunk k is combined
-        float f[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) f[q] = slot_field(cp, s0, q, TPX)[lp];
-        for (uint32_t k = 0; k < nch; ++k) {
-            float g[6];
-            if (k + 1 < nch) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) g[q] = slot_field(cp, s0 + k + 1, q, TPX)[lp];
-            }
-            const float Tk = f[4];
-            const int lk = __float_as_int(f[5]);
-            const float Tn = __fmul_rn(T, Tk);
-            if ((lk & (int)0x80000000) || Tn < kTMin) {
-                stop = (int)k;
-                break;
-            }
-            C0 = fmaf(T, f[0], C0);
-            C1 = fmaf(T, f[1], C1);
-            C2 = fmaf(T, f[2], C2);
-            D = fmaf(T, f[3], D);
-            T = Tn;
-            if (lk) last = lk;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) f[q] = g[q];
-        }
         const size_t gp = V.pix_base + (size_t)py * V.W + bp.px;
-        PixState st{stop, 0, T, C0, C1, C2, D, T, C0, C1, C2, D, last, 0};
-        if (stop >= 0) {
+        PixState st{stop[j], 0, T[j], C0[j], C1[j], C2[j], D[j], T[j], C0[j], C1[j], C2[j], D[j], last[j], 0};
+        if (stop[j] >= 0) {
             // the part of the stop chunk that holds the stop: the first checkpoint
             // whose transmittance is (within 1%) below the limit, or whose local walk
-            // had stopped; the walk resumes from the checkpoint before it
+            // had stopped; the walk resumes from the checkpoint before it.  The
+            // checkpoints' transmittances and flags are loaded together first.
             const uint2 rg = ranges[gt];
-            const int64_t rest = (int64_t)rg.y - (int64_t)rg.x - (int64_t)stop * cp.L;
+            const int64_t rest = (int64_t)rg.y - (int64_t)rg.x - (int64_t)stop[j] * cp.L;
             const int clen = (int)(rest < cp.L ? rest : cp.L);
             const int every = cp.L / kSub;
+            const uint32_t sl = s0 + (uint32_t)stop[j];
+            float Tm[kSub - 1];
+            int lm[kSub - 1];
+#pragma unroll
+            for (int m = 0; m < kSub - 1; ++m) {
+                const bool written = (m + 1) * every < clen; // else past the chunk's end
+                Tm[m] = written ? slot_group(cp, sl, m, 4, TPX)[lp] : 0.f;
+                lm[m] = written ? __float_as_int(slot_group(cp, sl, m, 5, TPX)[lp]) : 0;
+            }
             int m = 0;
-            for (; m < kSub - 1; ++m) {
-                if ((m + 1) * every >= clen) break; // checkpoint m lies past the chunk's end: not written
-                const uint32_t sl = s0 + (uint32_t)stop;
-                const float Tm = slot_group(cp, sl, m, 4, TPX)[lp];
-                const int lm = __float_as_int(slot_group(cp, sl, m, 5, TPX)[lp]);
-                if ((lm & (int)0x80000000) || __fmul_rn(T, Tm) < 1.01f * kTMin) break;
-                st.Tc = __fmul_rn(T, Tm);
-                st.Cc0 = fmaf(T, slot_group(cp, sl, m, 0, TPX)[lp], C0);
-                st.Cc1 = fmaf(T, slot_group(cp, sl, m, 1, TPX)[lp], C1);
-                st.Cc2 = fmaf(T, slot_group(cp, sl, m, 2, TPX)[lp], C2);
-                st.Dc = fmaf(T, slot_group(cp, sl, m, 3, TPX)[lp], D);
-                if (lm) st.lastc = lm;
+#pragma unroll
+            for (int mm = 0; mm < kSub - 1; ++mm) {
+                if (m != mm) break;
+                if ((mm + 1) * every >= clen) break;
+                if ((lm[mm] & (int)0x80000000) || __fmul_rn(T[j], Tm[mm]) < 1.01f * kTMin) break;
+                m = mm + 1;
+            }
+            if (m > 0) {
+                st.Tc = __fmul_rn(T[j], Tm[m - 1]);
+                st.Cc0 = fmaf(T[j], slot_group(cp, sl, m - 1, 0, TPX)[lp], C0[j]);
+                st.Cc1 = fmaf(T[j], slot_group(cp, sl, m - 1, 1, TPX)[lp], C1[j]);
+                st.Cc2 = fmaf(T[j], slot_group(cp, sl, m - 1, 2, TPX)[lp], C2[j]);
+                st.Dc = fmaf(T[j], slot_group(cp, sl, m - 1, 3, TPX)[lp], D[j]);
+                if (lm[m - 1]) st.lastc = lm[m - 1];
             }
             st.sub = m;
         }
         ps[gp] = st;
-        if (stop < 0) write_final(V, out, vi, final_T, n_contrib, bp.px, py, T, C0, C1, C2, D, last);
+        if (stop[j] < 0) write_final(V, out, vi, final_T, n_contrib, bp.px, py, T[j], C0[j], C1[j], C2[j], D[j], last[j]);
     }
 }
 
