@@ -608,60 +608,80 @@ combine_state_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp, const PixSta
     const int vi = view_of_tile(*vsp, gt);
     const ViewDesc &V = vsp->v[vi];
     const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
+    // Each slot before the stop chunk becomes (its contribution, T at its end);
+    // the stop chunk's slot was written by the exact walk.  Then, from the last
+    // chunk back, every slot gets the normalised sums of what lies after it.
+    // The lane's two pixels run together, and both loops load the next chunk's
+    // fields while handling the current one.
+    bool in[PPT];
+    int lp[PPT];
+    uint32_t top[PPT], n_fwd[PPT];
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         const int py = bp.py0 + j;
-        if (!(bp.px < V.W && py < V.H)) continue;
-        const int lp = bp.lp0 + j * TW;
-        const int stop = ps[V.pix_base + (size_t)py * V.W + bp.px].stop;
-        const uint32_t top = stop >= 0 ? (uint32_t)stop : nch - 1;
-        // each slot before the stop chunk becomes (its contribution, T at its end);
-        // the stop chunk's slot was written by the exact walk
-        // (both loops load the next chunk's fields while handling the current one)
-        float t = 1.f;
-        const uint32_t n_fwd = stop < 0 ? top + 1 : top;
-        {
-            float h[5];
-            if (n_fwd > 0) {
+        in[j] = bp.px < V.W && py < V.H;
+        lp[j] = bp.lp0 + j * TW;
+        const int stop = in[j] ? ps[V.pix_base + (size_t)py * V.W + bp.px].stop : -1;
+        top[j] = stop >= 0 ? (uint32_t)stop : nch - 1;
+        n_fwd[j] = !in[j] ? 0u : (stop < 0 ? top[j] + 1 : top[j]);
+    }
+    {
+        float t[PPT] = {1.f, 1.f}, h[PPT][5];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) h[q] = slot_field(cp, s0, q, TPX)[lp];
-            }
-            for (uint32_t k = 0; k < n_fwd; ++k) {
-                float nx[5];
-                if (k + 1 < n_fwd) {
+        for (int j = 0; j < PPT; ++j)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) nx[q] = slot_field(cp, s0 + k + 1, q, TPX)[lp];
-                }
-                const float tend = __fmul_rn(t, h[4]);
+            for (int q = 0; q < 5; ++q) h[j][q] = n_fwd[j] > 0 ? slot_field(cp, s0, q, TPX)[lp[j]] : 0.f;
+        const uint32_t n_max = max(n_fwd[0], n_fwd[1]);
+        for (uint32_t k = 0; k < n_max; ++k) {
+            float nx[PPT][5];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) slot_field(cp, s0 + k, q, TPX)[lp] = h[q] * t;
-                slot_field(cp, s0 + k, 4, TPX)[lp] = t - tend;
-                slot_field(cp, s0 + k, 5, TPX)[lp] = tend;
-                t = tend;
+            for (int j = 0; j < PPT; ++j)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) h[q] = nx[q];
+                for (int q = 0; q < 5; ++q)
+                    nx[j][q] = k + 1 < n_fwd[j] ? slot_field(cp, s0 + k + 1, q, TPX)[lp[j]] : 0.f;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                if (k >= n_fwd[j]) continue;
+                const float tend = __fmul_rn(t[j], h[j][4]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) slot_field(cp, s0 + k, q, TPX)[lp[j]] = h[j][q] * t[j];
+                slot_field(cp, s0 + k, 4, TPX)[lp[j]] = t[j] - tend;
+                slot_field(cp, s0 + k, 5, TPX)[lp[j]] = tend;
+                t[j] = tend;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) h[j][q] = nx[j][q];
             }
         }
-        float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        {
-            float h[6];
+    }
+    {
+        float acc[PPT][5], h[PPT][6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) h[q] = slot_field(cp, s0 + top, q, TPX)[lp];
-            for (int k = (int)top; k >= 0; --k) {
-                float nx[6];
-                if (k > 0) {
+        for (int j = 0; j < PPT; ++j) {
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) nx[q] = slot_field(cp, s0 + k - 1, q, TPX)[lp];
-                }
-                const float tend = h[5];
+            for (int q = 0; q < 5; ++q) acc[j][q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) h[j][q] = in[j] ? slot_field(cp, s0 + top[j], q, TPX)[lp[j]] : 0.f;
+        }
+        // k runs from the larger top down; pixel j joins at its own top
+        for (int k = (int)max(top[0], top[1]); k >= 0; --k) {
+            float nx[PPT][6];
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    nx[j][q] = (in[j] && k > 0 && k <= (int)top[j]) ? slot_field(cp, s0 + k - 1, q, TPX)[lp[j]] : 0.f;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                if (!in[j] || k > (int)top[j]) continue;
+                const float tend = h[j][5];
                 const float inv = tend > 0.f ? 1.f / tend : 0.f;
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    slot_field(cp, s0 + k, q, TPX)[lp] = acc[q] * inv;
-                    acc[q] += h[q];
+                    slot_field(cp, s0 + k, q, TPX)[lp[j]] = acc[j][q] * inv;
+                    acc[j][q] += h[j][q];
                 }
 #pragma unroll
-                for (int q = 0; q < 6; ++q) h[q] = nx[q];
+                for (int q = 0; q < 6; ++q) h[j][q] = nx[j][q];
             }
         }
     }
@@ -786,26 +806,33 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
             for (int q = n - 1; q >= 0; --q) {
                 const float4 a = sm.A[q];
                 const float4 b = sm.B[q];
-                const float4 c = sm.C[q];
                 const int pos = sm.Pos[q];
                 const float dx = a.x - fpx;
                 const float a2dx = __fmul_rn(a.z, dx);
+                // the 1/255 tests of both pixels first: a Gaussian that no pixel
+                // of the block takes costs the warp nothing more
+                float e2[PPT];
+                bool take[PPT];
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const float dy = a.y - (float)(bp.py0 + j);
+                    e2[j] = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy); // log2(o G), as forward
+                    take[j] = pos < last[j] && e2[j] >= kLog2AlphaMin;
+                }
+                if (!__any_sync(0xffffffffu, take[0] || take[1])) continue;
+                const float4 c = sm.C[q];
                 // v: sums over the lane's pixels of dp dx, dp dy, dp dx^2, dp dx dy,
                 // dp dy^2 (dp = dL/dpower), o dL/do, and w g_R, w g_G, w g_B, w g_D;
                 // the conic is applied per Gaussian in the chain rule that follows
                 float v[NACC];
 #pragma unroll
                 for (int m = 0; m < NACC; ++m) v[m] = 0.f;
-                bool any = false;
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    if (pos >= last[j]) continue;
+                    if (!take[j]) continue;
                     const float dy = a.y - (float)(bp.py0 + j);
-                    const float e2 = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy); // log2(o G), as forward
-                    if (e2 < kLog2AlphaMin) continue;
-                    const float oG = exp2_approx(e2);
+                    const float oG = exp2_approx(e2[j]);
                     const float alpha = fminf(kAlphaMax, oG);
-                    any = true;
                     T[j] = __fdividef(T[j], 1.f - alpha);
                     const float wgt = alpha * T[j];
                     const float cg = fmaf(c.x, gC0[j], fmaf(c.y, gC1[j], fmaf(c.z, gC2[j], fmaf(b.z, gD[j], gA[j]))));
@@ -826,12 +853,10 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                         v[4] = fmaf(dpy, dy, v[4]);
                     }
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    int vidx;
-                    bool valid;
-                    const float tot = reduce_scatter10(v, lane, vidx, valid);
-                    if (valid && tot != 0.f) atomicAdd((float *)(g2d + sm.Idx[q]) + grad_offset(vidx), tot);
-                }
+                int vidx;
+                bool valid;
+                const float tot = reduce_scatter10(v, lane, vidx, valid);
+                if (valid && tot != 0.f) atomicAdd((float *)(g2d + sm.Idx[q]) + grad_offset(vidx), tot);
             }
             __syncwarp();
             hi = lo;
