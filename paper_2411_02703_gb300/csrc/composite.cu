@@ -226,20 +226,29 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
             const float a2dx = __fmul_rn(a.z, dx);
             int qpos = 0;
             if (START) qpos = sm.Pos[q];
+            // the 1/255 tests of both pixels first (e2 = log2(o G); no test of a
+            // positive power: the conic is positive definite, so one is rounding
+            // at the centre)
+            float e2[PPT];
+            bool take[PPT];
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-                if (START && (done[k] || qpos < start[k])) continue;
                 const float dy = a.y - (float)(py0 + k);
-                // e2 = log2(o G); no test of a positive power: the conic is
-                // positive definite, so one is rounding at the centre
-                const float e2 = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy);
-                if (e2 < (START ? kLog2AlphaMin : thr[k])) continue; // alpha < 1/255, or finished
-                const float alpha = fminf(kAlphaMax, exp2_approx(e2));
+                e2[k] = gauss_exponent2(a2dx, a.w, b.x, b.y, dx, dy);
+                take[k] = e2[k] >= (START ? kLog2AlphaMin : thr[k]); // alpha >= 1/255, pixel not finished
+                if (START) take[k] = take[k] && !done[k] && qpos >= start[k];
+            }
+            if (!(take[0] || take[1])) continue;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!take[k]) continue;
+                const float alpha = fminf(kAlphaMax, exp2_approx(e2[k]));
                 const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
                     done[k] = true;
                     stopped[k] = true;
                     thr[k] = 1e30f;
+                    tdone = done[0] && done[1];
                     continue;
                 }
                 const float4 c = sm.C[q];
@@ -251,7 +260,6 @@ __device__ __forceinline__ void fwd_walk(const uint32_t *__restrict__ inst_vals,
                 T[k] = Tn;
                 last[k] = sm.Pos[q] + 1;
             }
-            tdone = done[0] && done[1];
         }
         __syncwarp();
         if (CKPT && next_ck < n_ck && base + B - lo == (uint32_t)(next_ck + 1) * (uint32_t)ck.every)
