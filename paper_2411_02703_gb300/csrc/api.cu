@@ -357,10 +357,8 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     }
     {
         Phase ph(ctx, LVIGS_PHASE_COMPACT, s);
-        launch_scan((const uint32_t *)st.tiles.p, nullptr, 1, (uint32_t *)ctx->pos.p, cnt + 0, nullptr, VN,
-                    (uint32_t *)ctx->scan_tmp.p, s);
-        launch_compact((const uint32_t *)st.tiles.p, (const uint32_t *)st.zbits.p, (const uint32_t *)ctx->pos.p,
-                       (uint32_t *)ctx->ck.p, (uint32_t *)ctx->cv.p, VN, s);
+        launch_compact_scan((const uint32_t *)st.tiles.p, (const uint32_t *)st.zbits.p, (uint32_t *)ctx->ck.p,
+                            (uint32_t *)ctx->cv.p, cnt + 0, VN, (uint32_t *)ctx->scan_tmp.p, s);
     }
     int r;
     {

@@ -143,9 +143,10 @@ void launch_scan(const uint32_t *in, const uint32_t *gather, int flag_only, uint
                  uint32_t *out_total, const uint32_t *n_dev, int64_t n_max, uint32_t *tmp,
                  cudaStream_t s);
 
-// Compaction of visible (tiles > 0) items: keys = zbits[i], vals = i.
-void launch_compact(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
-                    uint32_t *keys, uint32_t *vals, int64_t n, cudaStream_t s);
+// Compaction of the visible (tiles > 0) items in index order: keys = zbits[i],
+// vals = i; out_total receives their count.  tmp as for launch_scan.
+void launch_compact_scan(const uint32_t *tiles, const uint32_t *zbits, uint32_t *keys, uint32_t *vals,
+                         uint32_t *out_total, int64_t n, uint32_t *tmp, cudaStream_t s);
 
 // LSD radix sort of (key, value) pairs over bits [0, bits).  Stable.
 // n read from the device (n_dev), or n_max when n_dev is null.  Returns 1 when

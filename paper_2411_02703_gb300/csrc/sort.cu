@@ -103,31 +103,127 @@ scan_blocks_kernel(uint32_t *block_sums, uint32_t nb, uint32_t *out_total) {
     if (threadIdx.x == 0 && out_total) *out_total = carry;
 }
 
+// The block's tile moves between memory and registers through shared memory:
+// loads and stores stay coalesced (consecutive threads, consecutive items)
+// while each thread scans kScanItems consecutive items in registers, so one
+// block-wide scan of the thread sums gives all the offsets.
+constexpr int kScanPitch = kScanItems + 1; // conflict-free blocked reads
 __global__ void __launch_bounds__(kScanThreads)
 scan_down_kernel(const uint32_t *in, const uint32_t *gather, int flag_only, const uint32_t *n_dev,
                  uint32_t n_host, const uint32_t *block_offsets, uint32_t *out) {
+    __shared__ uint32_t tile[kScanThreads * kScanPitch];
     const uint32_t n = n_dev ? *n_dev : n_host;
     const uint32_t begin = blockIdx.x * (uint32_t)kScanTile;
     if (begin >= n) return;
-    const uint32_t end = min(begin + (uint32_t)kScanTile, n);
-    uint32_t carry = block_offsets[blockIdx.x];
-    for (uint32_t base = begin; base < end; base += kScanThreads) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t x = i < end ? scan_item(in, gather, flag_only, i) : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan_256(x, &tot);
-        if (i < end) out[i] = carry + ex;
-        carry += tot;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t r = (uint32_t)(j * kScanThreads + t); // tile-relative item
+        tile[(r / kScanItems) * kScanPitch + r % kScanItems] =
+            begin + r < n ? scan_item(in, gather, flag_only, begin + r) : 0u;
+    }
+    __syncthreads();
+    uint32_t x[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        x[j] = tile[t * kScanPitch + j];
+        sum += x[j];
+    }
+    uint32_t tot;
+    uint32_t run = block_offsets[blockIdx.x] + block_exclusive_scan_256(sum, &tot);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        tile[t * kScanPitch + j] = run;
+        run += x[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t r = (uint32_t)(j * kScanThreads + t);
+        if (begin + r < n) out[begin + r] = tile[(r / kScanItems) * kScanPitch + r % kScanItems];
     }
 }
 
-__global__ void compact_kernel(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
-                               uint32_t *keys, uint32_t *vals, uint32_t n) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (tiles[i] != 0u) {
-            const uint32_t p = pos[i];
-            keys[p] = zbits[i];
-            vals[p] = i;
+// The whole scan in one block of 1024 threads, for inputs of at most
+// kScanSingle items (one launch instead of three).
+constexpr int kScanSingle = 1024 * kScanItems;
+__global__ void __launch_bounds__(1024)
+scan_single_kernel(const uint32_t *in, const uint32_t *gather, int flag_only, const uint32_t *n_dev,
+                   uint32_t n_host, uint32_t *out, uint32_t *out_total) {
+    __shared__ uint32_t warp_sums[32];
+    const uint32_t n = n_dev ? min(*n_dev, n_host) : n_host;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t i0 = threadIdx.x * (uint32_t)kScanItems;
+    uint32_t x[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        x[j] = i0 + j < n ? scan_item(in, gather, flag_only, i0 + j) : 0u;
+        sum += x[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t ws = warp_sums[lane];
+        uint32_t wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_sums[lane] = wi - ws;
+        if (lane == 31 && out_total) *out_total = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_sums[warp] + inc - sum;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (i0 + j < n) out[i0 + j] = run;
+        run += x[j];
+    }
+}
+
+// Compaction of the visible items fused into the scan's last step: each
+// thread scans the visibility flags of its kScanItems consecutive items and
+// writes the (depth bits, item index) pairs of the visible ones at their
+// positions (index order).
+__global__ void __launch_bounds__(kScanThreads)
+compact_down_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ zbits, uint32_t n,
+                    const uint32_t *__restrict__ block_offsets, uint32_t *__restrict__ keys,
+                    uint32_t *__restrict__ vals) {
+    __shared__ uint32_t tile[kScanThreads * kScanPitch];
+    const uint32_t begin = blockIdx.x * (uint32_t)kScanTile;
+    if (begin >= n) return;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t r = (uint32_t)(j * kScanThreads + t);
+        tile[(r / kScanItems) * kScanPitch + r % kScanItems] = begin + r < n && tiles[begin + r] != 0u;
+    }
+    __syncthreads();
+    uint32_t flags = 0, sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const uint32_t f = tile[t * kScanPitch + j];
+        flags |= f << j;
+        sum += f;
+    }
+    uint32_t tot;
+    uint32_t run = block_offsets[blockIdx.x] + block_exclusive_scan_256(sum, &tot);
+    const uint32_t i0 = begin + (uint32_t)t * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (flags >> j & 1u) {
+            keys[run] = zbits[i0 + j];
+            vals[run] = i0 + j;
+            ++run;
         }
     }
 }
@@ -402,15 +498,25 @@ void launch_scan(const uint32_t *in, const uint32_t *gather, int flag_only, uint
         if (out_total) cudaMemsetAsync(out_total, 0, sizeof(uint32_t), s);
         return;
     }
+    if (n_max <= kScanSingle) {
+        scan_single_kernel<<<1, 1024, 0, s>>>(in, gather, flag_only, n_dev, (uint32_t)n_max, out, out_total);
+        return;
+    }
     scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, gather, flag_only, n_dev, (uint32_t)n_max, tmp);
     scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(tmp, nb, out_total);
     scan_down_kernel<<<nb, kScanThreads, 0, s>>>(in, gather, flag_only, n_dev, (uint32_t)n_max, tmp, out);
 }
 
-void launch_compact(const uint32_t *tiles, const uint32_t *zbits, const uint32_t *pos,
-                    uint32_t *keys, uint32_t *vals, int64_t n, cudaStream_t s) {
-    if (n <= 0) return;
-    compact_kernel<<<grid_stride_blocks(n, 256), 256, 0, s>>>(tiles, zbits, pos, keys, vals, (uint32_t)n);
+void launch_compact_scan(const uint32_t *tiles, const uint32_t *zbits, uint32_t *keys, uint32_t *vals,
+                         uint32_t *out_total, int64_t n, uint32_t *tmp, cudaStream_t s) {
+    const uint32_t nb = (uint32_t)((n + kScanTile - 1) / kScanTile);
+    if (nb == 0) {
+        cudaMemsetAsync(out_total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(tiles, nullptr, 1, nullptr, (uint32_t)n, tmp);
+    scan_blocks_kernel<<<1, kScanThreads, 0, s>>>(tmp, nb, out_total);
+    compact_down_kernel<<<nb, kScanThreads, 0, s>>>(tiles, zbits, (uint32_t)n, tmp, keys, vals);
 }
 
 size_t radix_tmp_words(int64_t n_max) { return (size_t)256 * rs_grid(n_max) + 256; }
