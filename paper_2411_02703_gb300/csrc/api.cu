@@ -413,7 +413,7 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
         launch_pair_keys(st.plan(), st.vs.total_tiles, (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
         st.order_in_alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p,
                                             (uint32_t *)st.pair_k2.p, (uint32_t *)st.pair_v2.p, cnt + 4,
-                                            st.pair_cap, 16, (uint32_t *)ctx->radix_tmp.p, s);
+                                            st.pair_cap, 8, (uint32_t *)ctx->radix_tmp.p, s);
         LV_CUDA(cudaMemsetAsync(st.stop_at.p, 0xff, (size_t)st.vs.total_pixels * 4, s));
     }
     return LVIGS_OK;
@@ -427,7 +427,7 @@ ChunkPlan backward_plan(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
     launch_bwd_pair_keys(st.vs, (const ViewSet *)st.vs_dev.p, cp, (const int32_t *)st.n_contrib.p,
                          (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
     const int alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, (uint32_t *)st.pair_k2.p,
-                                      (uint32_t *)st.pair_v2.p, cnt + 4, st.pair_cap, 11,
+                                      (uint32_t *)st.pair_v2.p, cnt + 4, st.pair_cap, 8,
                                       (uint32_t *)ctx->radix_tmp.p, s);
     cp.pair_order = (const uint32_t *)(alt ? st.pair_v2.p : st.pair_v.p);
     return cp;

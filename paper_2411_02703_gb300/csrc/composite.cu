@@ -905,9 +905,11 @@ __global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const u
                                  uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const uint32_t n = min(*n_pairs, pair_cap);
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        // 8-bit keys (one radix pass): chunks from the 255th on share the last
+        // bucket, in pair order; the order only schedules work
         const uint32_t t = pair_tile[p];
-        const uint32_t k = t < n_tiles ? p - chunk_base[t] : 0xffffu;
-        keys[p] = k < 0xffffu ? k : 0xffffu;
+        const uint32_t k = t < n_tiles ? p - chunk_base[t] : 255u;
+        keys[p] = k < 255u ? k : 255u;
         vals[p] = p;
     }
 }
@@ -915,7 +917,8 @@ __global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const u
 // Backward work order: (tile, chunk) pairs by decreasing expected walk, the
 // part of the chunk before the tile's furthest last contributor; the longest
 // items start first, which keeps the tail of the persistent kernel short.
-// One warp per pair; key = L - walk (0 first), L + 1 for pairs of no tile.
+// One warp per pair; key = (L - walk) scaled to 0..254 (0 first), 255 for
+// pairs of no tile: 8 bits, one radix pass.
 template <int TW, int TH>
 __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp,
                                      const int32_t *__restrict__ n_contrib, uint32_t *__restrict__ keys,
@@ -926,7 +929,7 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
         const uint32_t t = cp.pair_tile[p];
-        uint32_t key = (uint32_t)cp.L + 1u;
+        uint32_t key = 255u;
         if (t < vsp->total_tiles) {
             const uint32_t k = p - cp.chunk_base[t];
             const ViewDesc &V = vsp->v[view_of_tile(*vsp, t)];
@@ -939,7 +942,8 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
             }
             mx = __reduce_max_sync(0xffffffffu, mx);
             const int64_t walk = (int64_t)mx - (int64_t)k * cp.L;
-            key = (uint32_t)cp.L - (uint32_t)(walk < 0 ? 0 : (walk > cp.L ? cp.L : walk));
+            const uint32_t rest = (uint32_t)cp.L - (uint32_t)(walk < 0 ? 0 : (walk > cp.L ? cp.L : walk));
+            key = (uint32_t)(((uint64_t)rest * 254u) / (uint32_t)cp.L);
         }
         if (lane == 0) {
             keys[p] = key;

@@ -350,10 +350,7 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
             view_point_strict(vsp->v[vi], mx, my, mz, px, py, pz);
             front = L.ok && (pz > 0.2f);
             zbits[o] = __float_as_uint(pz);
-            if (!front) {
-                tiles[o] = 0;
-                rects[o] = make_uint2(0, 0);
-            }
+            if (!front) tiles[o] = 0; // (its rectangle is never read)
         }
         const uint32_t m = __ballot_sync(0xffffffffu, front);
         if (lane == 0) s_mask[w][vi] = m;
