@@ -269,6 +269,14 @@ def workload(name):
         params, cam, gt, lidar = small_scene()
         return dict(params=params, cams=[cam], levels=[0], gts=[gt], lidars=[lidar],
                     lam=0.0, lam_d=1.0)
+    if name.startswith("pyramid_"):
+        # pyramid_<N> : one keyframe rendered at pyramid levels 0, 1 and 2 from N Gaussians
+        n = int(name.split("_")[1])
+        params, phase = lidar_scene(n)
+        cam = trajectory_cameras(1, phase=phase)[0]
+        gt, li = target_images(cam, BASE_SEED + 100)
+        return dict(params=params, cams=[cam, cam, cam], levels=[0, 1, 2], gts=[gt, gt, gt],
+                    lidars=[li, li, li], lam=0.2, lam_d=0.1)
     if name.startswith("lidar_"):
         # lidar_<N>_<V>v : N Gaussians, V keyframes at mixed levels
         _, n, v = name.split("_")
