@@ -410,31 +410,80 @@ radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__r
 // --------------------------------------------------------------------------
 // Instance emission, ranges, debug keys.
 // --------------------------------------------------------------------------
-__global__ void emit_kernel(const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ sorted_idx,
-                            const uint32_t *__restrict__ offsets, const uint32_t *n_vis_dev,
-                            const uint2 *__restrict__ rects, uint32_t n_gauss,
-                            uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ inst_vals,
-                            uint64_t m_cap, uint32_t *status) {
+// A warp takes 32 consecutive items (in depth order) and writes all their
+// instances together: lane r of each round of 32 output positions finds its
+// item by a binary search over the warp's exclusive prefix (shuffles), so the
+// stores are coalesced and an item that covers many tiles does not hold one
+// lane while the others idle.
+__global__ void __launch_bounds__(256)
+emit_kernel(const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ sorted_idx,
+            const uint32_t *__restrict__ offsets, const uint32_t *n_vis_dev, const uint2 *__restrict__ rects,
+            uint32_t n_gauss, uint32_t *__restrict__ tile_ids, uint32_t *__restrict__ inst_vals, uint64_t m_cap,
+            uint32_t *status) {
     const uint32_t n = *n_vis_dev;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint32_t idx = sorted_idx[j];
-        const uint32_t vi = idx / n_gauss;
-        const uint2 rc = rects[idx];
-        const uint32_t x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu, y1 = rc.y >> 16;
-        const uint32_t base = vsp->v[vi].tile_base;
-        const uint32_t tx_n = (uint32_t)vsp->v[vi].tiles_x;
-        uint64_t pos = offsets[j];
-        const uint64_t cnt = (uint64_t)(x1 - x0) * (y1 - y0);
-        if (pos + cnt > m_cap) {
-            atomicOr(status, kStatusCapacity);
-            continue;
-        }
-        for (uint32_t ty = y0; ty < y1; ++ty)
-            for (uint32_t tx = x0; tx < x1; ++tx) {
-                tile_ids[pos] = base + ty * tx_n + tx;
-                inst_vals[pos] = idx;
-                ++pos;
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t j0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; j0 < n; j0 += n_warps * 32u) {
+        const uint32_t j = j0 + (uint32_t)lane;
+        uint32_t idx = 0, cnt = 0, x0 = 0, y0 = 0, w = 1, base = 0, txn = 0;
+        uint64_t pos0 = 0;
+        if (j < n) {
+            idx = sorted_idx[j];
+            const uint32_t vi = idx / n_gauss;
+            const uint2 rc = rects[idx];
+            x0 = rc.x & 0xffffu;
+            y0 = rc.y & 0xffffu;
+            w = (rc.x >> 16) - x0;
+            cnt = w * ((rc.y >> 16) - y0);
+            base = vsp->v[vi].tile_base;
+            txn = (uint32_t)vsp->v[vi].tiles_x;
+            pos0 = offsets[j];
+            if (pos0 + cnt > m_cap) { // the suffix of items past the capacity is dropped
+                atomicOr(status, kStatusCapacity);
+                cnt = 0;
             }
+        }
+        if (w == 0) w = 1;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t excl = incl - cnt;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const uint32_t start_lo = __shfl_sync(0xffffffffu, (uint32_t)pos0, 0);
+        const uint32_t start_hi = __shfl_sync(0xffffffffu, (uint32_t)(pos0 >> 32), 0);
+        const uint64_t start = ((uint64_t)start_hi << 32) | start_lo;
+        const float inv_w = 1.f / (float)w;
+        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+            const uint32_t r = r0 + (uint32_t)lane;
+            // the last lane k whose exclusive prefix is <= r (zero-count lanes share
+            // the prefix of the next item and are passed over)
+            int k = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, excl, k + step);
+                if (e <= r) k += step;
+            }
+            const uint32_t q = r - __shfl_sync(0xffffffffu, excl, k);
+            const uint32_t kw = __shfl_sync(0xffffffffu, w, k);
+            const float kinv = __shfl_sync(0xffffffffu, inv_w, k);
+            const uint32_t kx0 = __shfl_sync(0xffffffffu, x0, k);
+            const uint32_t ky0 = __shfl_sync(0xffffffffu, y0, k);
+            const uint32_t kbase = __shfl_sync(0xffffffffu, base, k);
+            const uint32_t ktxn = __shfl_sync(0xffffffffu, txn, k);
+            const uint32_t kidx = __shfl_sync(0xffffffffu, idx, k);
+            if (r < total) {
+                // row within the rectangle: q / w, from the float estimate corrected by one
+                uint32_t ty = (uint32_t)((float)q * kinv);
+                if (ty * kw > q) --ty;
+                if ((ty + 1) * kw <= q) ++ty;
+                const uint64_t p = start + r;
+                tile_ids[p] = kbase + (ky0 + ty) * ktxn + kx0 + (q - ty * kw);
+                inst_vals[p] = kidx;
+            }
+        }
     }
 }
 
