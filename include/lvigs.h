@@ -101,6 +101,11 @@ typedef struct {
 #define LVIGS_STEP_HOST_TARGETS 1 /* gt_rgb / lidar_depth are pinned HOST pointers, copied in */
 #define LVIGS_STEP_HOST_LOSS 2    /* losses is a HOST pointer; the call waits for the step */
 #define LVIGS_STEP_NO_GRAPH 4     /* enqueue kernels directly instead of replaying a CUDA graph */
+#define LVIGS_STEP_STAGED_TARGETS 8 /* targets were copied in by lvigs_stage_targets into staged_slot;
+                                      gt_rgb / lidar_depth are not read */
+
+/* Staging slots of lvigs_stage_targets (double buffering). */
+#define LVIGS_STAGE_SLOTS 2
 
 /* One batched training step over several keyframes at mixed pyramid levels. */
 typedef struct {
@@ -116,7 +121,24 @@ typedef struct {
     float *const *rgb_out;           /* optional host array of n_views device pointers, or NULL */
     float *const *depth_out;         /* optional, as rgb_out */
     float *const *alpha_out;         /* optional, as rgb_out */
+    int staged_slot;                 /* with LVIGS_STEP_STAGED_TARGETS: 0..LVIGS_STAGE_SLOTS-1 */
 } lvigs_batch;
+
+/* Copy the level-0 targets of a batched step (Sec. III-D: each keyframe's image
+ * and projected LiDAR depth) from pinned HOST memory into the context's
+ * staging slot `slot`, on `copy_stream`, so that the copy of the next step's
+ * targets runs while the current step computes.  gt_rgb[v] points to
+ * [3,H0,W0] float32 and lidar_depth[v] (array may be NULL: no LiDAR term) to
+ * [H0,W0] float32 (0 = no return), sizes from cameras[v].  The copy first
+ * waits, on copy_stream, for the last batched step that read this slot; a
+ * later lvigs_train_step_batched with LVIGS_STEP_STAGED_TARGETS and
+ * staged_slot = slot waits for the copy on its own stream and must describe
+ * the same number of views and sizes.  The host buffers must stay valid until
+ * the copy has completed (e.g. until that step returns with
+ * LVIGS_STEP_HOST_LOSS).  Errors: LVIGS_ERR_INVALID_ARG (slot, view count,
+ * camera or NULL pointer), LVIGS_ERR_OUT_OF_MEMORY, LVIGS_ERR_CUDA. */
+lvigs_status lvigs_stage_targets(lvigs_ctx *ctx, int slot, int n_views, const lvigs_camera *cameras,
+                                 const float *const *gt_rgb, const float *const *lidar_depth, void *copy_stream);
 
 /* ----------------------------------------------------------------------- */
 

@@ -16,6 +16,8 @@ LVIGS_MAX_LEVEL = 4
 STEP_HOST_TARGETS = 1
 STEP_HOST_LOSS = 2
 STEP_NO_GRAPH = 4
+STEP_STAGED_TARGETS = 8
+STAGE_SLOTS = 2
 
 STATUS = {0: "LVIGS_OK", 1: "LVIGS_ERR_INVALID_ARG", 2: "LVIGS_ERR_OUT_OF_MEMORY", 3: "LVIGS_ERR_CUDA",
           4: "LVIGS_ERR_CAPACITY", 5: "LVIGS_ERR_TIMEOUT", 6: "LVIGS_ERR_STATE"}
@@ -59,7 +61,7 @@ class Batch(ctypes.Structure):
                 ("lidar_depth", ctypes.POINTER(ctypes.c_void_p)), ("lambda_ssim", ctypes.c_float),
                 ("lambda_depth", ctypes.c_float), ("flags", ctypes.c_int), ("losses", ctypes.c_void_p),
                 ("rgb_out", ctypes.POINTER(ctypes.c_void_p)), ("depth_out", ctypes.POINTER(ctypes.c_void_p)),
-                ("alpha_out", ctypes.POINTER(ctypes.c_void_p))]
+                ("alpha_out", ctypes.POINTER(ctypes.c_void_p)), ("staged_slot", ctypes.c_int)]
 
 
 class ParamBuffers(ctypes.Structure):
@@ -94,6 +96,8 @@ SIGNATURES = {
     "lvigs_loss_noalloc": (_I, [_I, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
     "lvigs_pyramid_down": (_I, [_I, _I, _P, _P, _P, _P, _P]),
     "lvigs_train_step_batched": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Batch), ctypes.POINTER(Grads), _P]),
+    "lvigs_stage_targets": (_I, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Camera), ctypes.POINTER(_P),
+                                 ctypes.POINTER(_P), _P]),
     "lvigs_debug_keys": (_I, [_P, _I, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
     "lvigs_debug_state": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(_I), _P]),
     "lvigs_debug_exp_key": (_I, [_P, _P, ctypes.c_int64, _P]),

@@ -99,6 +99,7 @@ class Context:
         self._h = ctypes.c_void_p()
         L.check(self._lib.lvigs_create(ctypes.byref(self._h), ctypes.byref(cfg)), "lvigs_create")
         self.tile = (int(tile[0]), int(tile[1]))
+        self._copy_stream = None  # stream of stage_targets, created on first use
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -177,7 +178,7 @@ class Context:
 
     # -- batched path ------------------------------------------------------
     def _batch(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, grads, accumulate, host_targets,
-               host_loss, graph, outputs, losses):
+               host_loss, graph, outputs, losses, staged_slot=None):
         V = len(cams)
         g = gaussians_struct(params)
         if grads is None:
@@ -186,8 +187,9 @@ class Context:
         keep = []  # ctypes arrays referenced by the Batch struct
         camarr = (L.Camera * V)(*[camera_struct(c) for c in cams])
         lvl = (ctypes.c_int * V)(*[int(x) for x in levels])
-        gtp = (ctypes.c_void_p * V)(*[t.data_ptr() for t in gts])
-        lip = (ctypes.c_void_p * V)(*[t.data_ptr() if t is not None else None for t in lidars])
+        gtp = (ctypes.c_void_p * V)(*([t.data_ptr() for t in gts] if gts is not None else [None] * V))
+        lip = (ctypes.c_void_p * V)(*([t.data_ptr() if t is not None else None for t in lidars]
+                                      if lidars is not None else [None] * V))
         keep += [camarr, lvl, gtp, lip]
         if losses is None:
             losses = torch.zeros((V, 4), dtype=torch.float64,
@@ -201,7 +203,8 @@ class Context:
         b.lambda_ssim = float(lambda_ssim)
         b.lambda_depth = float(lambda_depth)
         b.flags = ((L.STEP_HOST_TARGETS if host_targets else 0) | (L.STEP_HOST_LOSS if host_loss else 0)
-                   | (0 if graph else L.STEP_NO_GRAPH))
+                   | (0 if graph else L.STEP_NO_GRAPH) | (L.STEP_STAGED_TARGETS if staged_slot is not None else 0))
+        b.staged_slot = int(staged_slot) if staged_slot is not None else 0
         b.losses = losses.data_ptr()
         if outputs is not None:
             for i, nm in enumerate(("rgb_out", "depth_out", "alpha_out")):
@@ -210,17 +213,41 @@ class Context:
                 setattr(b, nm, arr)
         return g, b, gs, grads, losses, keep
 
+    def stage_targets(self, cams, gts, lidars, slot):
+        """Copy level-0 targets from pinned CPU tensors into staging slot `slot`
+        (0 or 1) on the context's copy stream, after the last step that read the
+        slot; a later train_step_batched(..., staged_slot=slot) waits for the copy.
+        The tensors must stay alive until that step has run."""
+        V = len(cams)
+        if len(gts) != V or (lidars is not None and len(lidars) != V):
+            raise ValueError("one target (and LiDAR map) per camera")
+        for i, c in enumerate(cams):
+            shapes = [(gts[i], (3, c.H, c.W))] + ([(lidars[i], (c.H, c.W))] if lidars is not None else [])
+            for t, shp in shapes:
+                if (not isinstance(t, torch.Tensor) or t.is_cuda or not t.is_pinned() or t.dtype != torch.float32
+                        or not t.is_contiguous() or tuple(t.shape) != shp):
+                    raise ValueError(f"stage_targets takes pinned contiguous float32 CPU tensors of shape {shp}")
+        if self._copy_stream is None:
+            self._copy_stream = torch.cuda.Stream()
+        camarr = (L.Camera * V)(*[camera_struct(c) for c in cams])
+        gtp = (ctypes.c_void_p * V)(*[t.data_ptr() for t in gts])
+        lip = None if lidars is None else (ctypes.c_void_p * V)(*[t.data_ptr() for t in lidars])
+        self._chk(self._lib.lvigs_stage_targets(self._h, int(slot), V, camarr, gtp, lip,
+                                                ctypes.c_void_p(self._copy_stream.cuda_stream)),
+                  "lvigs_stage_targets")
+
     def train_step_batched(self, params, cams, levels, gts, lidars, lambda_ssim, lambda_depth, grads=None,
                            accumulate=False, host_targets=False, host_loss=False, graph=True, outputs=None,
-                           losses=None):
+                           losses=None, staged_slot=None):
         """One batched step (a10): render, loss and backward of every view.
 
         gts / lidars are level-0 targets (CUDA tensors, or pinned CPU tensors with
-        host_targets=True).  Returns (losses [V,4] float64, grads).
+        host_targets=True), or None with staged_slot = the slot a previous
+        stage_targets call filled.  Returns (losses [V,4] float64, grads).
         """
         g, b, gs, grads, losses, keep = self._batch(params, cams, levels, gts, lidars, lambda_ssim, lambda_depth,
                                                     grads, accumulate, host_targets, host_loss, graph, outputs,
-                                                    losses)
+                                                    losses, staged_slot)
         self._chk(self._lib.lvigs_train_step_batched(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(gs),
                                                      _stream()), "lvigs_train_step_batched")
         del keep

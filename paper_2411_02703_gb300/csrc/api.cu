@@ -98,10 +98,18 @@ struct lvigs_ctx {
     cudaEvent_t vs_event = nullptr, step_event = nullptr;
     bool step_pending = false;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    BatchKey graph_key;
-    bool graph_ok = false;
+    // one graph for steps with their own targets, one per staging slot
+    cudaGraphExec_t graph_exec[1 + LVIGS_STAGE_SLOTS] = {};
+    BatchKey graph_key[1 + LVIGS_STAGE_SLOTS];
+    bool graph_ok[1 + LVIGS_STAGE_SLOTS] = {};
     int kernels_per_step = 0;
+    // targets staged by lvigs_stage_targets: per slot the buffers, whether the
+    // LiDAR maps were staged, the sizes, and the copy-done / last-read events
+    DevBuf stg_gt[LVIGS_STAGE_SLOTS][kMaxViews], stg_li[LVIGS_STAGE_SLOTS][kMaxViews];
+    bool stg_has_li[LVIGS_STAGE_SLOTS] = {};
+    int stg_views[LVIGS_STAGE_SLOTS] = {};
+    int stg_w[LVIGS_STAGE_SLOTS][kMaxViews] = {}, stg_h[LVIGS_STAGE_SLOTS][kMaxViews] = {};
+    cudaEvent_t stg_ready[LVIGS_STAGE_SLOTS] = {}, stg_read[LVIGS_STAGE_SLOTS] = {};
 
     // map maintenance (append / prune) scratch, kept apart from the step's
     // buffers so that growing it does not invalidate the step's graph
@@ -493,6 +501,10 @@ lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->vs_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->step_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < LVIGS_STAGE_SLOTS && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&ctx->stg_ready[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stg_read[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         lvigs_destroy(ctx);
@@ -525,13 +537,22 @@ void lvigs_destroy(lvigs_ctx *ctx) {
     for (int v = 0; v < kMaxViews; ++v) {
         release(ctx, ctx->gt_stage[v]);
         release(ctx, ctx->lidar_stage[v]);
+        for (int k = 0; k < LVIGS_STAGE_SLOTS; ++k) {
+            release(ctx, ctx->stg_gt[k][v]);
+            release(ctx, ctx->stg_li[k][v]);
+        }
         for (int l = 0; l <= LVIGS_MAX_LEVEL; ++l) {
             release(ctx, ctx->pyr_rgb[v][l]);
             release(ctx, ctx->pyr_depth[v][l]);
         }
     }
-    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    for (cudaGraphExec_t ge : ctx->graph_exec)
+        if (ge) cudaGraphExecDestroy(ge);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int k = 0; k < LVIGS_STAGE_SLOTS; ++k) {
+        if (ctx->stg_ready[k]) cudaEventDestroy(ctx->stg_ready[k]);
+        if (ctx->stg_read[k]) cudaEventDestroy(ctx->stg_read[k]);
+    }
     for (auto &pe : ctx->prof_pending) {
         cudaEventDestroy(pe.second.first);
         cudaEventDestroy(pe.second.second);
@@ -802,7 +823,8 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
                           cudaStream_t s, bool eager) {
     RenderState &st = ctx->batch;
     const int V = b->n_views;
-    const bool host_tg = (b->flags & LVIGS_STEP_HOST_TARGETS) != 0;
+    const bool staged = (b->flags & LVIGS_STEP_STAGED_TARGETS) != 0;
+    const bool host_tg = !staged && (b->flags & LVIGS_STEP_HOST_TARGETS) != 0;
     // 1. targets at each view's level (Sec. III-D)
     const float *gt_l[kMaxViews];
     const float *li_l[kMaxViews];
@@ -810,8 +832,14 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     for (int v = 0; v < V; ++v) {
         const lvigs_camera &c = b->cameras[v];
         const size_t P0 = (size_t)c.width * c.height;
-        const float *gsrc = b->gt_rgb[v];
-        const float *lsrc = b->lidar_depth ? b->lidar_depth[v] : nullptr;
+        const float *gsrc = nullptr, *lsrc = nullptr;
+        if (staged) {
+            gsrc = (const float *)ctx->stg_gt[b->staged_slot][v].p;
+            lsrc = ctx->stg_has_li[b->staged_slot] ? (const float *)ctx->stg_li[b->staged_slot][v].p : nullptr;
+        } else {
+            gsrc = b->gt_rgb[v];
+            lsrc = b->lidar_depth ? b->lidar_depth[v] : nullptr;
+        }
         if (host_tg) {
             LV_TRY(ensure(ctx, ctx->gt_stage[v], 3 * P0 * 4));
             LV_CUDA(cudaMemcpyAsync(ctx->gt_stage[v].p, gsrc, 3 * P0 * 4, cudaMemcpyHostToDevice, s));
@@ -960,12 +988,19 @@ BatchKey make_key(const lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_ba
     addf(b->lambda_ssim);
     addf(b->lambda_depth);
     addp(b->losses);
+    const bool staged = (b->flags & LVIGS_STEP_STAGED_TARGETS) != 0;
+    if (staged) add((uint64_t)b->staged_slot);
     for (int v = 0; v < b->n_views; ++v) {
         add((uint64_t)b->cameras[v].width);
         add((uint64_t)b->cameras[v].height);
         add((uint64_t)b->levels[v]);
-        addp(b->gt_rgb[v]);
-        addp(b->lidar_depth ? b->lidar_depth[v] : nullptr);
+        if (staged) {
+            addp(ctx->stg_gt[b->staged_slot][v].p);
+            addp(ctx->stg_has_li[b->staged_slot] ? ctx->stg_li[b->staged_slot][v].p : nullptr);
+        } else {
+            addp(b->gt_rgb[v]);
+            addp(b->lidar_depth ? b->lidar_depth[v] : nullptr);
+        }
         addp(b->rgb_out ? b->rgb_out[v] : nullptr);
         addp(b->depth_out ? b->depth_out[v] : nullptr);
         addp(b->alpha_out ? b->alpha_out[v] : nullptr);
@@ -979,8 +1014,13 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
                                                  const lvigs_grads *gr, void *stream) {
     if (!ctx) return LVIGS_ERR_INVALID_ARG;
     LV_TRY(check_gauss(ctx, g));
-    if (!b || b->n_views < 1 || b->n_views > kMaxViews || !b->cameras || !b->levels || !b->gt_rgb || !b->losses)
+    const bool staged = b && (b->flags & LVIGS_STEP_STAGED_TARGETS) != 0;
+    if (!b || b->n_views < 1 || b->n_views > kMaxViews || !b->cameras || !b->levels || (!staged && !b->gt_rgb) ||
+        !b->losses)
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad batch description");
+    if (staged && (b->staged_slot < 0 || b->staged_slot >= LVIGS_STAGE_SLOTS ||
+                   ctx->stg_views[b->staged_slot] != b->n_views))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "staged slot does not hold this step's targets");
     if (!gr || (g->n > 0 && (!gr->d_means || !gr->d_log_scales || !gr->d_quats || !gr->d_opacity_logits ||
                              !gr->d_sh)))
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL gradient output");
@@ -990,7 +1030,13 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "n * n_views must be below 2^32");
     for (int v = 0; v < b->n_views; ++v) {
         LV_TRY(check_camera(ctx, &b->cameras[v], b->levels[v]));
-        if (!b->gt_rgb[v]) return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL target image");
+        if (staged) {
+            if (ctx->stg_w[b->staged_slot][v] != b->cameras[v].width ||
+                ctx->stg_h[b->staged_slot][v] != b->cameras[v].height)
+                return fail(ctx, LVIGS_ERR_INVALID_ARG, "staged target size differs from the camera");
+        } else if (!b->gt_rgb[v]) {
+            return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL target image");
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
     RenderState &st = ctx->batch;
@@ -1023,16 +1069,18 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
 
     const bool use_graph = !(b->flags & LVIGS_STEP_NO_GRAPH);
     BatchKey key = make_key(ctx, g, b, gr);
+    const int gi = staged ? 1 + b->staged_slot : 0; // which cached graph
+    if (staged) LV_CUDA(cudaStreamWaitEvent(s, ctx->stg_ready[b->staged_slot], 0));
     if (!use_graph || grow || st.m_cap == 0) {
         // eager step: sizes the instance capacity (waits once on the stream)
         LV_TRY(batched_body(ctx, g, b, gr, s, true));
     } else {
-        if (!ctx->graph_ok || !(key == ctx->graph_key)) {
-            if (ctx->graph_exec) {
-                cudaGraphExecDestroy(ctx->graph_exec);
-                ctx->graph_exec = nullptr;
+        if (!ctx->graph_ok[gi] || !(key == ctx->graph_key[gi])) {
+            if (ctx->graph_exec[gi]) {
+                cudaGraphExecDestroy(ctx->graph_exec[gi]);
+                ctx->graph_exec[gi] = nullptr;
             }
-            ctx->graph_ok = false;
+            ctx->graph_ok[gi] = false;
             // the capture stream waits for nothing; the graph is launched on `s`
             ctx->capturing = true;
             ctx->capture_short = false;
@@ -1054,28 +1102,64 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
                     }
                     ctx->kernels_per_step = kc;
                 }
-                e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+                e = cudaGraphInstantiate(&ctx->graph_exec[gi], graph, 0);
                 if (e == cudaSuccess) {
-                    ctx->graph_ok = true;
-                    ctx->graph_key = key;
+                    ctx->graph_ok[gi] = true;
+                    ctx->graph_key[gi] = key;
                 }
             }
             if (graph) cudaGraphDestroy(graph);
             cudaGetLastError();
         }
-        if (ctx->graph_ok) {
-            LV_CUDA(cudaGraphLaunch(ctx->graph_exec, s));
+        if (ctx->graph_ok[gi]) {
+            LV_CUDA(cudaGraphLaunch(ctx->graph_exec[gi], s));
         } else {
             LV_TRY(batched_body(ctx, g, b, gr, s, true));
         }
     }
     LV_CUDA(cudaEventRecord(ctx->step_event, s));
+    if (staged) LV_CUDA(cudaEventRecord(ctx->stg_read[b->staged_slot], s)); // the slot may be refilled after this
     ctx->step_pending = true;
     if (b->flags & LVIGS_STEP_HOST_LOSS) {
         LV_CUDA(cudaStreamSynchronize(s));
         std::memcpy(b->losses, ctx->host_losses, (size_t)b->n_views * 4 * sizeof(double));
     }
     LV_CUDA(cudaGetLastError());
+    return LVIGS_OK;
+}
+
+// Targets of a later batched step copied in from pinned host memory on a
+// second stream (double-buffered slots), so that the copy overlaps the step
+// before it.
+extern "C" lvigs_status lvigs_stage_targets(lvigs_ctx *ctx, int slot, int n_views, const lvigs_camera *cameras,
+                                            const float *const *gt_rgb, const float *const *lidar_depth,
+                                            void *copy_stream) {
+    if (!ctx) return LVIGS_ERR_INVALID_ARG;
+    if (slot < 0 || slot >= LVIGS_STAGE_SLOTS || n_views < 1 || n_views > kMaxViews || !cameras || !gt_rgb)
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad staging request");
+    if (ctx->capturing) return fail(ctx, LVIGS_ERR_STATE, "staging during a graph capture");
+    for (int v = 0; v < n_views; ++v) {
+        if (cameras[v].width <= 0 || cameras[v].height <= 0 || !gt_rgb[v] || (lidar_depth && !lidar_depth[v]))
+            return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad staged view");
+    }
+    cudaStream_t cs = (cudaStream_t)copy_stream;
+    // the previous reader of the slot must be done before it is overwritten
+    // (a buffer that grows is reallocated, which waits for the device)
+    LV_CUDA(cudaStreamWaitEvent(cs, ctx->stg_read[slot], 0));
+    for (int v = 0; v < n_views; ++v) {
+        const size_t P0 = (size_t)cameras[v].width * cameras[v].height;
+        LV_TRY(ensure(ctx, ctx->stg_gt[slot][v], 3 * P0 * 4));
+        LV_CUDA(cudaMemcpyAsync(ctx->stg_gt[slot][v].p, gt_rgb[v], 3 * P0 * 4, cudaMemcpyHostToDevice, cs));
+        if (lidar_depth) {
+            LV_TRY(ensure(ctx, ctx->stg_li[slot][v], P0 * 4));
+            LV_CUDA(cudaMemcpyAsync(ctx->stg_li[slot][v].p, lidar_depth[v], P0 * 4, cudaMemcpyHostToDevice, cs));
+        }
+        ctx->stg_w[slot][v] = cameras[v].width;
+        ctx->stg_h[slot][v] = cameras[v].height;
+    }
+    ctx->stg_views[slot] = n_views;
+    ctx->stg_has_li[slot] = lidar_depth != nullptr;
+    LV_CUDA(cudaEventRecord(ctx->stg_ready[slot], cs));
     return LVIGS_OK;
 }
 

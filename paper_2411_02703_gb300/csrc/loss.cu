@@ -11,6 +11,8 @@
 // Each thread filters a run of four outputs from a 14-sample window held in
 // registers (rows in the horizontal pass, columns in the vertical one), so a
 // staged sample is read from shared memory about 3.5 times instead of 11.
+// The next channel's tile is copied in (cp.async) while the current one's
+// vertical pass runs.
 // A one-block-per-view kernel sums the tile partials in a fixed order
 // (deterministic) into the four loss terms.
 // Pass 2 applies the adjoint window to those derivative maps and adds the
@@ -61,52 +63,29 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
     return s;
 }
 
-// Stage a tile of `img` (plus halo, zero outside the image) into dst[LS][LS+1];
-// every load is issued before the first store.
+// Stage a tile of `img` (plus halo) into dst[LS][LS+1] asynchronously
+// (cp.async, 4 bytes per element, zero-filled outside the image): the copies
+// land while the block goes on computing; cp_async_wait<0> and a barrier make
+// them visible.
 constexpr int kStageIt = (LS * LS + kThreads - 1) / kThreads;
-__device__ __forceinline__ void stage(const float *__restrict__ img, int W, int H, int tx, int ty,
-                                      float (*dst)[LS + 1]) {
-    float v[kStageIt];
-#pragma unroll
-    for (int j = 0; j < kStageIt; ++j) {
-        const int i = threadIdx.x + j * kThreads;
-        const int r = i / LS, c = i - r * LS;
-        const int gx = tx * LT + c - HALO, gy = ty * LT + r - HALO;
-        v[j] = (i < LS * LS && gx >= 0 && gx < W && gy >= 0 && gy < H) ? __ldg(img + (size_t)gy * W + gx) : 0.f;
-    }
-#pragma unroll
-    for (int j = 0; j < kStageIt; ++j) {
-        const int i = threadIdx.x + j * kThreads;
-        if (i < LS * LS) dst[i / LS][i % LS] = v[j];
-    }
-}
-
-// stage() of three images at once (all their loads in flight together).
-__device__ __forceinline__ void stage3(const float *__restrict__ i0, const float *__restrict__ i1,
-                                       const float *__restrict__ i2, int W, int H, int tx, int ty,
-                                       float (*dst)[LS][LS + 1]) {
-    float v[3][kStageIt];
-#pragma unroll
-    for (int j = 0; j < kStageIt; ++j) {
-        const int i = threadIdx.x + j * kThreads;
-        const int r = i / LS, c = i - r * LS;
-        const int gx = tx * LT + c - HALO, gy = ty * LT + r - HALO;
-        const bool ok = i < LS * LS && gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const size_t q = ok ? (size_t)gy * W + gx : 0;
-        v[0][j] = ok ? __ldg(i0 + q) : 0.f;
-        v[1][j] = ok ? __ldg(i1 + q) : 0.f;
-        v[2][j] = ok ? __ldg(i2 + q) : 0.f;
-    }
+__device__ __forceinline__ void stage_async(const float *__restrict__ img, int W, int H, int tx, int ty,
+                                            float (*dst)[LS + 1]) {
 #pragma unroll
     for (int j = 0; j < kStageIt; ++j) {
         const int i = threadIdx.x + j * kThreads;
         if (i < LS * LS) {
-            dst[0][i / LS][i % LS] = v[0][j];
-            dst[1][i / LS][i % LS] = v[1][j];
-            dst[2][i / LS][i % LS] = v[2][j];
+            const int r = i / LS, c = i - r * LS;
+            const int gx = tx * LT + c - HALO, gy = ty * LT + r - HALO;
+            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const float *src = ok ? img + (size_t)gy * W + gx : img;
+            const uint32_t d = (uint32_t)__cvta_generic_to_shared(&dst[r][c]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0));
         }
     }
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 __global__ void __launch_bounds__(kThreads, 4)
 loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *__restrict__ partials) {
@@ -127,6 +106,12 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
     float l1 = 0.f, ssim = 0.f, dsum = 0.f, dcnt = 0.f;
     float *G = gmaps + lv.gmap_base[vi];
 
+    // the next channel is copied in while the current one's vertical pass runs
+    if (lam != 0.f) {
+        stage_async(lv.rgb[vi], W, H, tx, ty, sx);
+        stage_async(lv.gt[vi], W, H, tx, ty, sy);
+        cp_async_commit();
+    }
     for (int ch = 0; ch < 3; ++ch) {
         const float *x = lv.rgb[vi] + ch * HW;
         const float *y = lv.gt[vi] + ch * HW;
@@ -138,9 +123,7 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
             }
             continue;
         }
-        __syncthreads();
-        stage(x, W, H, tx, ty, sx);
-        stage(y, W, H, tx, ty, sy);
+        cp_async_wait<0>();
         __syncthreads();
         // L1 from the staged samples (zero outside the image on both sides)
 #pragma unroll
@@ -180,6 +163,12 @@ loss_pass1_kernel(LossViews lv, Window win, float *__restrict__ gmaps, double *_
             }
         }
         __syncthreads();
+        // sx, sy are free now: copy the next channel in
+        if (ch + 1 < 3) {
+            stage_async(x + HW, W, H, tx, ty, sx);
+            stage_async(y + HW, W, H, tx, ty, sy);
+            cp_async_commit();
+        }
         // vertical pass: this thread's run of four pixels
         float mom[5][RUN];
 #pragma unroll
@@ -306,9 +295,12 @@ loss_pass2_kernel(LossViews lv, Window win, const float *__restrict__ gmaps,
 #pragma unroll
         for (int o = 0; o < RUN; ++o) s1[o] = s2[o] = s12[o] = 0.f;
         if (lam != 0.f) {
-            __syncthreads();
-            stage3(G + (size_t)(0 * 3 + ch) * HW, G + (size_t)(1 * 3 + ch) * HW, G + (size_t)(2 * 3 + ch) * HW, W, H,
-                   tx, ty, sg);
+            if (ch == 0) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) stage_async(G + (size_t)(m * 3) * HW, W, H, tx, ty, sg[m]);
+                cp_async_commit();
+            }
+            cp_async_wait<0>();
             __syncthreads();
             for (int task = t; task < kRowTasks; task += kThreads) {
                 const int r = task / (LT / RUN), c0 = (task % (LT / RUN)) * RUN;
@@ -327,6 +319,12 @@ loss_pass2_kernel(LossViews lv, Window win, const float *__restrict__ gmaps,
                 }
             }
             __syncthreads();
+            // sg is free now: copy the next channel's maps in during the vertical pass
+            if (ch + 1 < 3) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) stage_async(G + (size_t)(m * 3 + ch + 1) * HW, W, H, tx, ty, sg[m]);
+                cp_async_commit();
+            }
             float *outs[3] = {s1, s2, s12};
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
