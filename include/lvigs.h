@@ -103,6 +103,9 @@ typedef struct {
 #define LVIGS_STEP_NO_GRAPH 4     /* enqueue kernels directly instead of replaying a CUDA graph */
 #define LVIGS_STEP_STAGED_TARGETS 8 /* targets were copied in by lvigs_stage_targets into staged_slot;
                                       gt_rgb / lidar_depth are not read */
+#define LVIGS_STEP_HOST_LOSS_ASYNC 16 /* losses is a pinned (page-locked) HOST pointer that the step's
+                                        kernels write directly; the call does not wait (order a later
+                                        read with an event on the stream) */
 
 /* Staging slots of lvigs_stage_targets (double buffering). */
 #define LVIGS_STAGE_SLOTS 2
@@ -117,7 +120,8 @@ typedef struct {
     float lambda_ssim;               /* lambda of Eq. (11) */
     float lambda_depth;              /* lambda_d of Eq. (10) */
     int flags;                       /* LVIGS_STEP_* */
-    double *losses;                  /* [n_views,4]: total, L1, mean SSIM, depth L1 */
+    double *losses;                  /* [n_views,4]: total, L1, mean SSIM, depth L1 (device memory
+                                        unless a HOST_LOSS flag says otherwise) */
     float *const *rgb_out;           /* optional host array of n_views device pointers, or NULL */
     float *const *depth_out;         /* optional, as rgb_out */
     float *const *alpha_out;         /* optional, as rgb_out */

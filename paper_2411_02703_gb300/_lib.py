@@ -17,6 +17,7 @@ STEP_HOST_TARGETS = 1
 STEP_HOST_LOSS = 2
 STEP_NO_GRAPH = 4
 STEP_STAGED_TARGETS = 8
+STEP_HOST_LOSS_ASYNC = 16
 STAGE_SLOTS = 2
 
 STATUS = {0: "LVIGS_OK", 1: "LVIGS_ERR_INVALID_ARG", 2: "LVIGS_ERR_OUT_OF_MEMORY", 3: "LVIGS_ERR_CUDA",

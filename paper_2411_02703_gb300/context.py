@@ -191,9 +191,16 @@ class Context:
         lip = (ctypes.c_void_p * V)(*([t.data_ptr() if t is not None else None for t in lidars]
                                       if lidars is not None else [None] * V))
         keep += [camarr, lvl, gtp, lip]
+        host_async = False
         if losses is None:
             losses = torch.zeros((V, 4), dtype=torch.float64,
                                  device="cpu" if host_loss else params["means"].device)
+        elif not losses.is_cuda and not host_loss:
+            # written by the step's kernels through the page-locked mapping; read it
+            # after an event recorded behind the step
+            if not losses.is_pinned() or losses.dtype != torch.float64 or not losses.is_contiguous():
+                raise ValueError("host losses without host_loss=True must be a pinned contiguous float64 tensor")
+            host_async = True
         b = L.Batch()
         b.n_views = V
         b.cameras = camarr
@@ -203,7 +210,8 @@ class Context:
         b.lambda_ssim = float(lambda_ssim)
         b.lambda_depth = float(lambda_depth)
         b.flags = ((L.STEP_HOST_TARGETS if host_targets else 0) | (L.STEP_HOST_LOSS if host_loss else 0)
-                   | (0 if graph else L.STEP_NO_GRAPH) | (L.STEP_STAGED_TARGETS if staged_slot is not None else 0))
+                   | (0 if graph else L.STEP_NO_GRAPH) | (L.STEP_STAGED_TARGETS if staged_slot is not None else 0)
+                   | (L.STEP_HOST_LOSS_ASYNC if host_async else 0))
         b.staged_slot = int(staged_slot) if staged_slot is not None else 0
         b.losses = losses.data_ptr()
         if outputs is not None:
@@ -243,7 +251,10 @@ class Context:
 
         gts / lidars are level-0 targets (CUDA tensors, or pinned CPU tensors with
         host_targets=True), or None with staged_slot = the slot a previous
-        stage_targets call filled.  Returns (losses [V,4] float64, grads).
+        stage_targets call filled.  losses may be a pinned CPU tensor without
+        host_loss: the step's kernels then write it directly and the call
+        returns at once (read it after an event recorded behind the step).
+        Returns (losses [V,4] float64, grads).
         """
         g, b, gs, grads, losses, keep = self._batch(params, cams, levels, gts, lidars, lambda_ssim, lambda_depth,
                                                     grads, accumulate, host_targets, host_loss, graph, outputs,

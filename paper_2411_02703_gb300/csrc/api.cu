@@ -91,7 +91,7 @@ struct lvigs_ctx {
     RenderState batch;
     DevBuf gt_stage[kMaxViews], lidar_stage[kMaxViews];
     DevBuf pyr_rgb[kMaxViews][LVIGS_MAX_LEVEL + 1], pyr_depth[kMaxViews][LVIGS_MAX_LEVEL + 1];
-    DevBuf img_rgb, img_depth, img_alpha, d_rgb, d_depth, losses_dev;
+    DevBuf img_rgb, img_depth, img_alpha, d_rgb, d_depth;
     double *host_losses = nullptr;       // pinned [kMaxViews * 4]
     uint32_t *host_batch_counters = nullptr; // pinned [4]
     ViewSet *vs_staging = nullptr;       // pinned
@@ -529,7 +529,7 @@ void lvigs_destroy(lvigs_ctx *ctx) {
     release_state(ctx, ctx->batch);
     DevBuf *shared[] = {&ctx->pos, &ctx->ck, &ctx->cv, &ctx->ck2, &ctx->cv2, &ctx->scan_tmp, &ctx->radix_tmp,
                         &ctx->status, &ctx->g2d, &ctx->loss_tmp, &ctx->stats, &ctx->img_rgb, &ctx->img_depth,
-                        &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->losses_dev, &ctx->mp_pts,
+                        &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->mp_pts,
                         &ctx->mp_col, &ctx->mp_keep, &ctx->mp_offs, &ctx->mp_keys, &ctx->mp_vals, &ctx->mp_keys2,
                         &ctx->mp_vals2, &ctx->mp_scan, &ctx->mp_radix, &ctx->mp_cells, &ctx->mp_logs,
                         &ctx->mp_small, &ctx->mp_tmp};
@@ -885,7 +885,6 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     LV_TRY(ensure(ctx, ctx->img_alpha, TP * 4));
     LV_TRY(ensure(ctx, ctx->d_rgb, 3 * TP * 4));
     LV_TRY(ensure(ctx, ctx->d_depth, TP * 4));
-    LV_TRY(ensure(ctx, ctx->losses_dev, kMaxViews * 4 * sizeof(double)));
     ViewImages im{};
     ViewGrads vg{};
     LossViews lv{};
@@ -910,7 +909,10 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         lv.lidar[v] = li_l[v];
         lv.d_rgb[v] = (float *)vg.d_rgb[v];
         lv.d_depth[v] = (float *)vg.d_depth[v];
-        lv.loss_out[v] = (double *)ctx->losses_dev.p + 4 * v;
+        // the loss kernel writes each view's terms where they are read: the
+        // caller's buffer (device, or pinned host with HOST_LOSS_ASYNC) or the
+        // context's pinned host copy (HOST_LOSS); no copy engine is involved
+        lv.loss_out[v] = ((b->flags & LVIGS_STEP_HOST_LOSS) ? ctx->host_losses : b->losses) + 4 * v;
     }
     lv.total_tiles = ltiles;
     lv.lambda_ssim = b->lambda_ssim;
@@ -928,12 +930,6 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         Phase ph(ctx, LVIGS_PHASE_LOSS, s);
         launch_loss(lv, ctx->loss_tmp.p, s);
     }
-    if (b->flags & LVIGS_STEP_HOST_LOSS)
-        LV_CUDA(cudaMemcpyAsync(ctx->host_losses, ctx->losses_dev.p, (size_t)V * 4 * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
-    else
-        LV_CUDA(cudaMemcpyAsync(b->losses, ctx->losses_dev.p, (size_t)V * 4 * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
     // 5. a6 + a7
     const int64_t VN = (int64_t)st.P.n * V;
     LV_TRY(ensure(ctx, ctx->g2d, (size_t)VN * sizeof(GGrad)));
@@ -1021,6 +1017,20 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
     if (staged && (b->staged_slot < 0 || b->staged_slot >= LVIGS_STAGE_SLOTS ||
                    ctx->stg_views[b->staged_slot] != b->n_views))
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "staged slot does not hold this step's targets");
+    if (!(b->flags & LVIGS_STEP_HOST_LOSS)) {
+        // the loss kernel writes b->losses itself: it must be device memory, or
+        // page-locked host memory with HOST_LOSS_ASYNC
+        cudaPointerAttributes pa{};
+        const cudaError_t pe = cudaPointerGetAttributes(&pa, b->losses);
+        cudaGetLastError();
+        const bool host_async = (b->flags & LVIGS_STEP_HOST_LOSS_ASYNC) != 0;
+        const bool ok = pe == cudaSuccess && (host_async ? pa.type == cudaMemoryTypeHost
+                                                         : (pa.type == cudaMemoryTypeDevice ||
+                                                            pa.type == cudaMemoryTypeManaged));
+        if (!ok)
+            return fail(ctx, LVIGS_ERR_INVALID_ARG,
+                        host_async ? "losses must be page-locked host memory" : "losses must be device memory");
+    }
     if (!gr || (g->n > 0 && (!gr->d_means || !gr->d_log_scales || !gr->d_quats || !gr->d_opacity_logits ||
                              !gr->d_sh)))
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "NULL gradient output");

@@ -86,3 +86,25 @@ def test_staging_errors(setup):
         lv.stage_targets(cams, gts, lis, 2)
     torch.cuda.synchronize()
     lv.close()
+
+
+def test_async_host_losses(setup):
+    """Losses written by the step's kernels into pinned host memory (no wait in
+    the call) equal the synchronous host read-back."""
+    P, dp, cams, levels, sets = setup
+    lv = P.Context(tile=(16, 16))
+    gts, lis = sets[0]
+    for _ in range(2):
+        ref, _ = lv.train_step_batched(dp, cams, levels, gts, lis, 0.2, 0.1, host_targets=True, host_loss=True)
+    host = torch.zeros((len(cams), 4), dtype=torch.float64).pin_memory()
+    ev = torch.cuda.Event()
+    for _ in range(2):
+        lv.train_step_batched(dp, cams, levels, gts, lis, 0.2, 0.1, host_targets=True, losses=host)
+        ev.record(torch.cuda.current_stream())
+        ev.synchronize()
+        assert torch.equal(host, ref)
+    with pytest.raises(ValueError):  # pageable host memory cannot be written by a kernel
+        lv.train_step_batched(dp, cams, levels, gts, lis, 0.2, 0.1, host_targets=True,
+                              losses=torch.zeros((len(cams), 4), dtype=torch.float64))
+    torch.cuda.synchronize()
+    lv.close()
