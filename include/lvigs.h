@@ -184,8 +184,10 @@ lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
  * SSIM with an 11x11 Gaussian window (sigma 1.5), zero padding,
  * C1 = 0.01^2, C2 = 0.03^2, averaged over channels and pixels; L_d is the
  * mean |depth - lidar| over pixels with lidar > 0 (0 if none).
- * loss_out: 4 device doubles (total, L1, mean SSIM, L_d).  d_rgb / d_depth
- * receive dL/drgb and dL/ddepth (either may be NULL to skip gradients). */
+ * loss_out: 4 doubles (total, L1, mean SSIM, L_d) in device memory or
+ * page-locked host memory (written by the kernel; LVIGS_ERR_INVALID_ARG for
+ * anything else).  d_rgb / d_depth receive dL/drgb and dL/ddepth (either may
+ * be NULL to skip gradients). */
 lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
                         const float *depth, const float *gt_rgb, const float *lidar_depth,
                         float lambda_ssim, float lambda_depth, double *loss_out, float *d_rgb,

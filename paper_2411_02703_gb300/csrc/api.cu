@@ -671,6 +671,8 @@ lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
         return fail(ctx, LVIGS_ERR_INVALID_ARG, "bad loss arguments");
     if (lidar_depth && !depth) return fail(ctx, LVIGS_ERR_INVALID_ARG, "lidar_depth given without depth");
     if (!(lambda_ssim >= 0.f && lambda_ssim <= 1.f)) return fail(ctx, LVIGS_ERR_INVALID_ARG, "lambda_ssim outside [0,1]");
+    if (!kernel_writable(loss_out))
+        return fail(ctx, LVIGS_ERR_INVALID_ARG, "loss_out must be device or page-locked host memory");
     LossViews lv{};
     lv.n_views = 1;
     lv.W[0] = width;

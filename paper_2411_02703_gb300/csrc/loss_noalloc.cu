@@ -91,6 +91,8 @@ extern "C" lvigs_status lvigs_loss_noalloc(int width, int height, const float *r
     lv.lambda_ssim = lambda_ssim;
     lv.lambda_depth = lambda_depth;
     if (loss_tmp_bytes(lv) > kScratchBytes) return LVIGS_ERR_CAPACITY;
+    // the loss kernel writes loss_out itself: device or page-locked host memory
+    if (!kernel_writable(loss_out)) return LVIGS_ERR_INVALID_ARG;
     void *scratch = nullptr;
     const lvigs_status st = scratch_address(&scratch);
     if (st != LVIGS_OK) return st;

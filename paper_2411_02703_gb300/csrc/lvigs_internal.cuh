@@ -115,6 +115,16 @@ __device__ __forceinline__ float exp2_approx(float x) {
 
 } // namespace lvigs
 
+// May a kernel write through p?  Device or managed memory, or page-locked
+// host memory (mapped into the device's address space).  Host-only query.
+inline bool kernel_writable(const void *p) {
+    cudaPointerAttributes pa{};
+    const cudaError_t e = cudaPointerGetAttributes(&pa, p);
+    cudaGetLastError();
+    return e == cudaSuccess &&
+           (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged || pa.type == cudaMemoryTypeHost);
+}
+
 // Kernel launchers (defined in the .cu files, called from the host API).
 namespace lvigs {
 
