@@ -21,7 +21,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["lvigs_create", "lvigs_destroy", "lvigs_render", "lvigs_backward", "lvigs_loss",
                      "lvigs_pyramid_down", "lvigs_train_step_batched", "lvigs_debug_keys", "lvigs_sync_status",
-                     "lvigs_release_view", "lvigs_last_error"]:
+                     "lvigs_release_view", "lvigs_last_error", "lvigs_stage_targets", "lvigs_adam_step",
+                     "lvigs_append_gaussians", "lvigs_prune_gaussians", "lvigs_loss_noalloc"]:
         assert required in names
 
 
@@ -59,6 +60,7 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.lvigs_sync_status(None, None) == 1
     assert lib.lvigs_release_view(None, 0) == 1
     assert lib.lvigs_pyramid_down(1, 1, None, None, None, None, None) == 1
+    assert lib.lvigs_stage_targets(None, 0, 1, None, None, None, None) == 1
     bad = _lib.Config(12, 12, 0, 0)
     h_ = ctypes.c_void_p()
     assert lib.lvigs_create(ctypes.byref(h_), ctypes.byref(bad)) == 1
