@@ -135,14 +135,15 @@ def preprocess(params, cam: Camera, tile=(16, 16)):
     out = dict(z_f=np.zeros(n, np.float32), uv_f=np.zeros((n, 2), np.float32),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                tiles=np.zeros(n, np.uint32), uv=np.zeros((n, 2)), conic=np.zeros((n, 3)),
-               opacity=np.zeros(n), rgb=np.zeros((n, 3)), depth=np.zeros(n), conic_f=np.zeros((n, 3)))
+               opacity=np.zeros(n), rgb=np.zeros((n, 3)), depth=np.zeros(n), conic_f=np.zeros((n, 3)),
+               rgb_margin=np.zeros(n))
     c = cam._c()
     rc = _load().orc_preprocess(
         ctypes.c_int64(n), _p(means), _p(ls), _p(q), _p(ol), _p(sh), ctypes.c_int(K),
         ctypes.c_int(deg), ctypes.byref(c), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
         _p(out["z_f"]), _p(out["uv_f"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]),
         _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]), _p(out["depth"]),
-        _p(out["conic_f"]))
+        _p(out["conic_f"]), _p(out["rgb_margin"]))
     if rc:
         raise ValueError(f"orc_preprocess failed ({rc})")
     out["tiles_x"] = (cam.W + tile[0] - 1) // tile[0]

@@ -272,6 +272,7 @@ typedef struct {
     double dir[3], dirlen, dirn[3];
     double Y[16], dY[16][3];
     double rgb_raw[3], rgb[3];
+    double rgb_margin;    /* min over channels of |rgb_raw| / (0.5 + sum |sh Y|) */
 } g64_t;
 
 static void value_stage(const float *m, const float *ls, const float *q, float ol, const float *sh,
@@ -341,11 +342,17 @@ static void value_stage(const float *m, const float *ls, const float *q, float o
     for (int i = 0; i < 3; ++i) g->dirn[i] = g->dir[i] / g->dirlen;
     sh_basis(g->dirn[0], g->dirn[1], g->dirn[2], g->Y, g->dY);
     int nk = (deg + 1) * (deg + 1);
+    g->rgb_margin = INFINITY;
     for (int ch = 0; ch < 3; ++ch) {
-        double acc = 0;
-        for (int k = 0; k < nk; ++k) acc += (double)sh[k * 3 + ch] * g->Y[k];
+        double acc = 0, mag = 0.5;
+        for (int k = 0; k < nk; ++k) {
+            acc += (double)sh[k * 3 + ch] * g->Y[k];
+            mag += fabs((double)sh[k * 3 + ch] * g->Y[k]);
+        }
         g->rgb_raw[ch] = acc + 0.5;
         g->rgb[ch] = g->rgb_raw[ch] < 0 ? 0 : g->rgb_raw[ch];
+        const double m = fabs(g->rgb_raw[ch]) / mag;
+        if (m < g->rgb_margin) g->rgb_margin = m;
     }
     (void)K;
 }
@@ -354,6 +361,8 @@ static void value_stage(const float *m, const float *ls, const float *q, float o
 /* a1: preprocess one view.                                                  */
 /* Key outputs (float/int): z, u, v, radius, rect[4], tiles_touched.         */
 /* Value outputs (double):  uv[2], conic[3], opacity, rgb[3], depth.         */
+/* rgb_margin (optional): distance of the SH colour's clamp at 0, relative to */
+/* the magnitude of its terms (min over channels; INFINITY when culled).      */
 /* conic_f[3] (optional): the inverse of the key stage's binary32 covariance */
 /* (its binary32 a, b, c over its binary32 determinant), taken in binary64:  */
 /* the conic a binary32 compositing stage starts from, for the error         */
@@ -364,7 +373,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
                    const orc_camera *cam, int tile_w, int tile_h,
                    float *z_f, float *uv_f, int32_t *radius, int32_t *rect, uint32_t *tiles,
                    double *uv, double *conic, double *opacity, double *rgb, double *depth,
-                   double *conic_f) {
+                   double *conic_f, double *rgb_margin) {
     if (n < 0 || tile_w <= 0 || tile_h <= 0 || sh_degree < 0 || sh_degree > 3 ||
         sh_stride_k < (sh_degree + 1) * (sh_degree + 1))
         return ORC_ERR_ARG;
@@ -390,6 +399,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
                 conic_f[3 * i] = conic_f[3 * i + 1] = conic_f[3 * i + 2] = 0;
             }
         }
+        if (rgb_margin) rgb_margin[i] = INFINITY;
         if (!k.visible) {
             uv[2 * i] = uv[2 * i + 1] = 0;
             conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0;
@@ -404,6 +414,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
         opacity[i] = g.opacity;
         for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = g.rgb[ch];
         depth[i] = g.p[2];
+        if (rgb_margin) rgb_margin[i] = g.rgb_margin;
     }
     return ORC_OK;
 }
