@@ -556,3 +556,23 @@ def test_render_margin_allowance_covers_binary32_evaluation():
     print(f"  binary32 decision flips at {flips} pixels, all within the allowance "
           f"({plain_beyond} beyond the plain margin)")
     assert flips > 0
+
+
+def test_colour_clamp_margin_closed_form():
+    """The SH colour's clamp margin: |0.5 + sum sh Y| over 0.5 + sum |sh Y|,
+    the smallest over channels.  Degree 0 (Y_00 = 1/(2 sqrt(pi))): a colour c in
+    [0, 1] has raw = c, terms 0.5 + |c - 0.5|."""
+    W, H, f = 32, 32, 40.0
+    cam = O.Camera(np.eye(3), np.zeros(3), f, f, 16.0, 16.0, W, H)
+    cols = [[0.0, 0.5, 1.0], [0.25, 0.9, 0.6]]
+    p = one_gaussian_params([[0, 0, 4.0], [0.5, 0, 5.0]], [math.log(0.2)] * 2, [1.0, 1.0], cols)
+    pre = O.preprocess(p, cam)
+    for i in range(len(cols)):
+        c = p["sh"][i, 0, :].astype(np.float64)  # the binary32 band-0 coefficients
+        raw = 0.5 + c / math.sqrt(4 * math.pi)
+        want = (np.abs(raw) / (0.5 + np.abs(c / math.sqrt(4 * math.pi)))).min()
+        assert abs(pre["rgb_margin"][i] - want) <= 1e-12
+    assert pre["rgb_margin"][0] < 1e-7  # a black channel sits on the clamp
+    # a culled Gaussian has no clamp
+    p2 = one_gaussian_params([[0, 0, -4.0]], [math.log(0.2)], [1.0], [[0.5, 0.5, 0.5]])
+    assert np.isinf(O.preprocess(p2, cam)["rgb_margin"][0])
