@@ -76,6 +76,11 @@ def num_threads() -> int:
     return int(_load().orc_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Threads of the following oracle calls (OpenMP)."""
+    _load().orc_set_num_threads(ctypes.c_int(int(n)))
+
+
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 

@@ -60,6 +60,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following oracle calls (for a single-core timing). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Pyramid level camera (Sec. III-D): level l halves the image l times.      */
 /* A level-l pixel covers a 2^l x 2^l block of level-0 pixels; with pixels   */
