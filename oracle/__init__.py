@@ -134,8 +134,17 @@ def _params(params):
             sh.shape[1], int(params["sh_degree"]))
 
 
-def preprocess(params, cam: Camera, tile=(16, 16)):
-    """a1 for one view at the camera's own resolution."""
+def preprocess(params, cam: Camera, tile=(16, 16), screen="key"):
+    """a1 for one view at the camera's own resolution.
+
+    ``screen`` chooses the screen-space Gaussian the composited values
+    describe: ``"key"`` (the default) takes the key stage's binary32 centre and
+    depth and the binary64 inverse of its binary32 covariance, the projection
+    of Eq. (7) that also decides the tile lists; ``"f64"`` recomputes the
+    projection in binary64, a smooth function of the parameters for the
+    finite-difference checks of the gradients."""
+    if screen not in ("key", "f64"):
+        raise ValueError(f"screen must be 'key' or 'f64', not {screen!r}")
     n, means, ls, q, ol, sh, K, deg = _params(params)
     out = dict(z_f=np.zeros(n, np.float32), uv_f=np.zeros((n, 2), np.float32),
                radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
@@ -148,7 +157,7 @@ def preprocess(params, cam: Camera, tile=(16, 16)):
         ctypes.c_int(deg), ctypes.byref(c), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
         _p(out["z_f"]), _p(out["uv_f"]), _p(out["radius"]), _p(out["rect"]), _p(out["tiles"]),
         _p(out["uv"]), _p(out["conic"]), _p(out["opacity"]), _p(out["rgb"]), _p(out["depth"]),
-        _p(out["conic_f"]), _p(out["rgb_margin"]))
+        _p(out["conic_f"]), _p(out["rgb_margin"]), ctypes.c_int(1 if screen == "key" else 0))
     if rc:
         raise ValueError(f"orc_preprocess failed ({rc})")
     out["tiles_x"] = (cam.W + tile[0] - 1) // tile[0]
@@ -179,27 +188,30 @@ def tile_ranges(keys, n_tiles: int, tile_base: int = 0):
     return r
 
 
-def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None):
+def _allowance_inputs(pre):
+    uv_f, conic_f = pre.get("uv_f"), pre.get("conic_f")
+    if uv_f is None or conic_f is None:
+        return None, None
+    return np.ascontiguousarray(uv_f, np.float32), np.ascontiguousarray(conic_f, np.float64)
+
+
+def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None, close_margin=-np.inf, flip=False):
     """a5: binary64 compositing.  ``sel_tiles`` limits the work to some tiles.
 
     ``margin`` is, per pixel, the smallest relative distance of any of its
-    threshold tests to the threshold; when ``pre`` carries the key stage's
-    binary32 centre (``uv_f``) and covariance inverse (``conic_f``), the
-    distance of the alpha, o G and T tests is net of the deviation binary32
-    inputs and evaluation may cause (see orc_render)."""
-    P = W * H
+    threshold tests to the threshold, net of the deviation binary32 inputs and
+    evaluation may cause (see orc_render).  ``n_close`` counts the tests whose
+    margin is at most ``close_margin``; with ``flip`` each of them takes the
+    other branch, which gives the other result the same arithmetic may
+    legitimately reach."""
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), alpha=np.zeros((H, W)),
                final_T=np.ones((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               margin=np.full((H, W), np.inf), signature=np.zeros((H, W), np.uint64))
+               margin=np.full((H, W), np.inf), signature=np.zeros((H, W), np.uint64),
+               n_close=np.zeros((H, W), np.int32))
     sel = None if sel_tiles is None else np.ascontiguousarray(sel_tiles, np.int32)
     if sel is not None and sel.shape[0] == 0:
         return out
-    uv_f, conic_f = pre.get("uv_f"), pre.get("conic_f")
-    if uv_f is None or conic_f is None:
-        uv_f = conic_f = None
-    else:
-        uv_f = np.ascontiguousarray(uv_f, np.float32)
-        conic_f = np.ascontiguousarray(conic_f, np.float64)
+    uv_f, conic_f = _allowance_inputs(pre)
     v = np.ascontiguousarray(vals, np.uint32)
     rg = np.ascontiguousarray(ranges, np.uint32)
     rc = _load().orc_render(
@@ -208,15 +220,19 @@ def render(pre, vals, ranges, W, H, tile=(16, 16), sel_tiles=None):
         _p(v), _p(rg), ctypes.c_int(0 if sel is None else sel.shape[0]), _p(sel),
         _p(out["rgb"]), _p(out["depth"]), _p(out["alpha"]), _p(out["final_T"]),
         _p(out["n_contrib"]), _p(out["margin"]), _p(out["signature"]),
-        _p(uv_f), _p(conic_f))
+        _p(uv_f), _p(conic_f), ctypes.c_double(close_margin), ctypes.c_int(1 if flip else 0),
+        _p(out["n_close"]))
     if rc:
         raise ValueError(f"orc_render failed ({rc})")
-    del P
     return out
 
 
-def loss(img, gt, depth, lidar, lam: float, lam_d: float, grads: bool = True):
-    """a8: (loss, l1, mean_ssim, depth_l1), d_img, d_depth, all binary64."""
+def loss(img, gt, depth, lidar, lam: float, lam_d: float, grads: bool = True,
+         kink_margin: float = -1.0, depth_kink_margin: float = -1.0, flip: bool = False):
+    """a8: (loss, l1, mean_ssim, depth_l1), d_img, d_depth, all binary64.
+
+    With ``flip`` an L1 residual within ``kink_margin`` (colour) or
+    ``depth_kink_margin`` (depth) of zero takes the other sign in the gradients."""
     img = np.ascontiguousarray(img, np.float64)
     gt = np.ascontiguousarray(gt, np.float64)
     depth = np.ascontiguousarray(depth, np.float64)
@@ -227,14 +243,17 @@ def loss(img, gt, depth, lidar, lam: float, lam_d: float, grads: bool = True):
     d_depth = np.zeros_like(depth) if grads else None
     rc = _load().orc_loss(ctypes.c_int(W), ctypes.c_int(H), _p(img), _p(gt), _p(depth), _p(lidar),
                           ctypes.c_double(lam), ctypes.c_double(lam_d), _p(terms), _p(d_img),
-                          _p(d_depth))
+                          _p(d_depth), ctypes.c_double(kink_margin), ctypes.c_double(depth_kink_margin),
+                          ctypes.c_int(1 if flip else 0))
     if rc:
         raise ValueError(f"orc_loss failed ({rc})")
     return terms, d_img, d_depth
 
 
-def backward_render(pre, vals, ranges, W, H, d_rgb, d_depth, d_alpha=None, tile=(16, 16)):
-    """a6: per-Gaussian (du, dv, dA, dB, dC, dopacity, drgb[3], ddepth)."""
+def backward_render(pre, vals, ranges, W, H, d_rgb, d_depth, d_alpha=None, tile=(16, 16),
+                    close_margin=-np.inf, flip=False):
+    """a6: per-Gaussian (du, dv, dA, dB, dC, dopacity, drgb[3], ddepth), over the
+    walk of ``render`` with the same ``close_margin`` / ``flip``."""
     n = pre["tiles"].shape[0]
     g2 = np.zeros((n, 10))
     d_rgb = np.ascontiguousarray(d_rgb, np.float64)
@@ -244,7 +263,9 @@ def backward_render(pre, vals, ranges, W, H, d_rgb, d_depth, d_alpha=None, tile=
         ctypes.c_int(W), ctypes.c_int(H), ctypes.c_int(tile[0]), ctypes.c_int(tile[1]),
         ctypes.c_int64(n), _p(pre["uv"]), _p(pre["conic"]), _p(pre["opacity"]), _p(pre["rgb"]),
         _p(pre["depth"]), _p(np.ascontiguousarray(vals, np.uint32)),
-        _p(np.ascontiguousarray(ranges, np.uint32)), _p(d_rgb), _p(d_depth), _p(d_alpha), _p(g2))
+        _p(np.ascontiguousarray(ranges, np.uint32)), _p(d_rgb), _p(d_depth), _p(d_alpha), _p(g2),
+        *(_p(a) for a in _allowance_inputs(pre)), ctypes.c_double(close_margin),
+        ctypes.c_int(1 if flip else 0))
     if rc:
         raise ValueError(f"orc_backward_render failed ({rc})")
     return g2
@@ -290,18 +311,21 @@ def pyramid(rgb, depth, level: int):
     return np.asarray(rgb, np.float64), np.asarray(depth, np.float64)
 
 
-def render_view(params, cam0: Camera, level: int = 0, tile=(16, 16), sel_tiles=None):
-    """a1-a5 for one view at pyramid level ``level``."""
+def render_view(params, cam0: Camera, level: int = 0, tile=(16, 16), sel_tiles=None, screen="key",
+                close_margin=-np.inf, flip=False):
+    """a1-a5 for one view at pyramid level ``level`` (``screen``: see
+    ``preprocess``; ``close_margin``, ``flip``: see ``render``)."""
     cam = level_camera(cam0, level)
-    pre = preprocess(params, cam, tile)
+    pre = preprocess(params, cam, tile, screen)
     keys, vals = build_keys(pre)
     n_tiles = pre["tiles_x"] * pre["tiles_y"]
     ranges = tile_ranges(keys, n_tiles)
-    img = render(pre, vals, ranges, cam.W, cam.H, tile, sel_tiles)
+    img = render(pre, vals, ranges, cam.W, cam.H, tile, sel_tiles, close_margin, flip)
     return dict(cam=cam, pre=pre, keys=keys, vals=vals, ranges=ranges, **img)
 
 
-def train_step(params, cams, levels, gts, lidars, lam, lam_d, tile=(16, 16)):
+def train_step(params, cams, levels, gts, lidars, lam, lam_d, tile=(16, 16), screen="key",
+               close_margin=-np.inf, flip=False, kink_margin=-1.0, depth_kink_margin=-1.0):
     """One hot-path pass over several views: render, loss and gradients.
 
     ``gts`` / ``lidars`` are level-0 targets; each view's targets are brought
@@ -311,11 +335,12 @@ def train_step(params, cams, levels, gts, lidars, lam, lam_d, tile=(16, 16)):
     grads = zero_grads(params)
     out = []
     for cam0, lvl, gt0, li0 in zip(cams, levels, gts, lidars):
-        r = render_view(params, cam0, lvl, tile)
+        r = render_view(params, cam0, lvl, tile, screen=screen, close_margin=close_margin, flip=flip)
         gt, li = pyramid(gt0, li0, lvl)
-        terms, d_img, d_depth = loss(r["rgb"], gt, r["depth"], li, lam, lam_d)
+        terms, d_img, d_depth = loss(r["rgb"], gt, r["depth"], li, lam, lam_d, True,
+                                     kink_margin, depth_kink_margin, flip)
         g2 = backward_render(r["pre"], r["vals"], r["ranges"], r["cam"].W, r["cam"].H,
-                             d_img, d_depth, None, tile)
+                             d_img, d_depth, None, tile, close_margin, flip)
         backward_preprocess(params, r["cam"], r["pre"], g2, grads)
         out.append(dict(terms=terms, render=r, grad2d=g2, gt=gt, lidar=li))
     return out, grads

@@ -370,6 +370,14 @@ static void value_stage(const float *m, const float *ls, const float *q, float o
 /* a1: preprocess one view.                                                  */
 /* Key outputs (float/int): z, u, v, radius, rect[4], tiles_touched.         */
 /* Value outputs (double):  uv[2], conic[3], opacity, rgb[3], depth.         */
+/* screen_key selects which screen-space Gaussian the values describe:      */
+/*   1  the key stage's own: its binary32 centre (u, v) and depth z, and the  */
+/*      binary64 inverse of its binary32 covariance (the same projection,    */
+/*      Eq. 7, that decides the tile lists; the paper's pipeline computes it */
+/*      once, in binary32);                                                  */
+/*   0  the projection recomputed in binary64 (a smooth function of the      */
+/*      parameters, for finite-difference checks of the gradients).          */
+/* Opacity and colour are binary64 in both.                                  */
 /* rgb_margin (optional): distance of the SH colour's clamp at 0, relative to */
 /* the magnitude of its terms (min over channels; INFINITY when culled).      */
 /* conic_f[3] (optional): the inverse of the key stage's binary32 covariance */
@@ -382,7 +390,7 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
                    const orc_camera *cam, int tile_w, int tile_h,
                    float *z_f, float *uv_f, int32_t *radius, int32_t *rect, uint32_t *tiles,
                    double *uv, double *conic, double *opacity, double *rgb, double *depth,
-                   double *conic_f, double *rgb_margin) {
+                   double *conic_f, double *rgb_margin, int screen_key) {
     if (n < 0 || tile_w <= 0 || tile_h <= 0 || sh_degree < 0 || sh_degree > 3 ||
         sh_stride_k < (sh_degree + 1) * (sh_degree + 1))
         return ORC_ERR_ARG;
@@ -418,11 +426,19 @@ int orc_preprocess(int64_t n, const float *means, const float *log_scales, const
         g64_t g;
         value_stage(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity_logits[i],
                     sh + (size_t)i * sh_stride_k * 3, sh_stride_k, sh_degree, cam, &g);
-        uv[2 * i] = g.u; uv[2 * i + 1] = g.v;
-        conic[3 * i] = g.conic[0]; conic[3 * i + 1] = g.conic[1]; conic[3 * i + 2] = g.conic[2];
+        if (screen_key) {
+            uv[2 * i] = (double)k.u; uv[2 * i + 1] = (double)k.v;
+            conic[3 * i] = (double)k.c / (double)k.det;
+            conic[3 * i + 1] = -(double)k.b / (double)k.det;
+            conic[3 * i + 2] = (double)k.a / (double)k.det;
+            depth[i] = (double)k.z;
+        } else {
+            uv[2 * i] = g.u; uv[2 * i + 1] = g.v;
+            conic[3 * i] = g.conic[0]; conic[3 * i + 1] = g.conic[1]; conic[3 * i + 2] = g.conic[2];
+            depth[i] = g.p[2];
+        }
         opacity[i] = g.opacity;
         for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = g.rgb[ch];
-        depth[i] = g.p[2];
         if (rgb_margin) rgb_margin[i] = g.rgb_margin;
     }
     return ORC_OK;
@@ -488,20 +504,38 @@ int orc_tile_ranges(int64_t m, const uint64_t *keys, uint32_t tile_base, int n_t
 
 /* ------------------------------------------------------------------------ */
 /* a5: front-to-back compositing (Eq. 3, 4, 5, 6) of a pixel over its tile's */
-/* sorted list.  Also reports the smallest relative distance of any test to  */
-/* its threshold, so callers can excuse pixels where binary32 arithmetic may */
-/* legitimately take the other branch.                                       */
+/* sorted list.  One walk serves both the images and their gradients, so the */
+/* two take the same decisions.                                              */
 /*                                                                           */
-/* With uv_f / conic_f (the binary32 centre of the key stage and the conic   */
-/* of its binary32 covariance) the distance of each test on alpha, o G and T */
-/* is net of an allowance for binary32: the exponent moves by                */
+/* Per Gaussian, in list order: power = -(A dx^2 + C dy^2)/2 - B dx dy       */
+/* (skipped if positive), alpha = min(0.99, o e^power) (Eq. 6), skipped if   */
+/* alpha < 1/255, and the walk stops before a Gaussian that would take T     */
+/* below 1e-4.                                                               */
+/*                                                                           */
+/* The walk also reports the smallest relative distance ("margin") of any    */
+/* test to its threshold, so callers can tell pixels where binary32          */
+/* arithmetic may legitimately take the other branch.  With uv_f / conic_f   */
+/* (the binary32 centre of the key stage and the conic of its binary32       */
+/* covariance) the distance of each test on alpha, o G and T is net of an    */
+/* allowance for binary32: the exponent moves by                             */
 /*   d_in  = |power(uv_f, conic_f) - power(uv, conic)|                       */
-/* (the deviation the binary32 inputs force, evaluated in binary64) plus     */
-/*   d_ev  = 16 u (scale + 1),  u = 2^-24,                                   */
-/* for the rounding of evaluating it and of the exponential, and alpha and   */
-/* o G move by the same amount relatively (first order).  T's relative       */
-/* allowance grows by alpha / (1 - alpha) times that, plus 2 u, per blended  */
-/* Gaussian.  The power > 0 test keeps its plain distance |power| / scale.   */
+/* (the deviation the binary32 inputs force, evaluated in binary64; zero     */
+/* when the values already are the key stage's) plus                         */
+/*   d_ev  = 16 u (scale + |ln o| + 1),  u = 2^-24,                          */
+/* for the rounding of evaluating it in binary32 (the conic from the         */
+/* covariance, the offsets, products and sums, the logarithm of the binary32 */
+/* opacity) and of the exponential, and alpha and o G move by the same       */
+/* amount relatively (first order).  T's relative allowance grows by         */
+/* alpha / (1 - alpha) times that, plus 2 u, per blended Gaussian.  The      */
+/* power > 0 test can only go the other way at binary64 rounding, where a    */
+/* binary32 evaluation has no such test at all: its margin is 0 when |power| */
+/* is within 64 binary64 ulps of the terms' scale and does not count         */
+/* otherwise.                                                                */
+/*                                                                           */
+/* "close" tests are those whose margin is at most close_margin.  With       */
+/* flip = 1 every close test takes the other branch: the result is the other */
+/* outcome the same arithmetic may legitimately give (first order: every     */
+/* close call at once).                                                      */
 /* ------------------------------------------------------------------------ */
 #define ALPHA_MAX 0.99
 #define ALPHA_MIN (1.0 / 255.0)
@@ -510,74 +544,167 @@ int orc_tile_ranges(int64_t m, const uint64_t *keys, uint32_t tile_base, int n_t
 static double rel_margin(double x, double thr) { return fabs(x - thr) / fabs(thr); }
 
 #define U32 (1.0 / 16777216.0)
+#define U64 (1.0 / 9007199254740992.0)
+
+typedef struct {
+    uint32_t g;
+    uint32_t pos;          /* position in the tile's list */
+    double alpha, T, G, dx, dy;
+    int clamped;
+} contrib_t;
+
+typedef struct {
+    const double *uv, *conic, *opacity;
+    const float *uv_f;     /* optional: allowance of the binary32 inputs */
+    const double *conic_f;
+    double close_margin;   /* tests with margin <= this are close */
+    int flip;              /* close tests take the other branch */
+} walk_in;
+
+typedef struct {
+    contrib_t *lst;        /* contributors in list order (grown on demand) */
+    size_t cap, cnt;
+    double T, margin;
+    int32_t last, nclose;
+    uint64_t sig;          /* FNV-1a of the contributing positions */
+} walk_out;
+
+/* Walk one pixel over vals[s, e).  Returns 0, or 1 if memory ran out. */
+static int walk_pixel(const walk_in *in, const uint32_t *vals, uint32_t s, uint32_t e, int px,
+                      int py, walk_out *w) {
+    const int allow = in->uv_f && in->conic_f;
+    double T = 1.0, margin = INFINITY, eT = 0; /* eT: relative allowance of T */
+    int32_t last = 0, nclose = 0;
+    uint64_t sig = 1469598103934665603ull;
+    w->cnt = 0;
+    for (uint32_t j = s; j < e; ++j) {
+        uint32_t g = vals[j];
+        double dx = in->uv[2 * g] - px, dy = in->uv[2 * g + 1] - py;
+        double A = in->conic[3 * g], B = in->conic[3 * g + 1], Cc = in->conic[3 * g + 2];
+        double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
+        double scale = 0.5 * (fabs(A) * dx * dx + fabs(Cc) * dy * dy) + fabs(B * dx * dy);
+        double o = in->opacity[g];
+        /* power > 0: only at binary64 rounding */
+        int skip_pos = power > 0;
+        if (scale > 0 && fabs(power) <= 64.0 * U64 * scale) {
+            if (0.0 < margin) margin = 0.0;
+            if (0.0 <= in->close_margin) {
+                ++nclose;
+                if (in->flip) skip_pos = !skip_pos;
+            }
+        }
+        if (skip_pos) continue;
+        double da = 16.0 * U32 * (scale + fabs(log(o)) + 1.0); /* relative allowance of o G, alpha */
+        if (allow) {
+            double fx = (double)in->uv_f[2 * g] - px, fy = (double)in->uv_f[2 * g + 1] - py;
+            double Af = in->conic_f[3 * g], Bf = in->conic_f[3 * g + 1], Cf = in->conic_f[3 * g + 2];
+            double pf = -0.5 * (Af * fx * fx + Cf * fy * fy) - Bf * fx * fy;
+            da += fabs(pf - power);
+        }
+        double G = exp(power);
+        double oG = o * G;
+        /* the 0.99 clamp */
+        int clamped = !(oG < ALPHA_MAX);
+        double mc = rel_margin(oG, ALPHA_MAX) - da;
+        if (mc < margin) margin = mc;
+        if (mc <= in->close_margin) {
+            ++nclose;
+            if (in->flip) clamped = !clamped;
+        }
+        double alpha = clamped ? ALPHA_MAX : oG;
+        /* the 1/255 cut */
+        int take = alpha >= ALPHA_MIN;
+        double ma = rel_margin(alpha, ALPHA_MIN) - da;
+        if (ma < margin) margin = ma;
+        if (ma <= in->close_margin) {
+            ++nclose;
+            if (in->flip) take = !take;
+        }
+        if (!take) continue;
+        /* the 1e-4 stop */
+        double Tn = T * (1.0 - alpha);
+        eT += alpha / (1.0 - alpha) * da + 2.0 * U32;
+        int stop = Tn < T_MIN;
+        double mt = rel_margin(Tn, T_MIN) - eT;
+        if (mt < margin) margin = mt;
+        if (mt <= in->close_margin) {
+            ++nclose;
+            if (in->flip) stop = !stop;
+        }
+        if (stop) break;
+        if (w->cnt == w->cap) {
+            size_t nc = w->cap ? 2 * w->cap : 64;
+            contrib_t *nl = (contrib_t *)realloc(w->lst, sizeof(contrib_t) * nc);
+            if (!nl) return 1;
+            w->lst = nl;
+            w->cap = nc;
+        }
+        contrib_t *c = &w->lst[w->cnt++];
+        c->g = g; c->pos = j - s; c->alpha = alpha; c->T = T; c->G = G; c->dx = dx; c->dy = dy;
+        c->clamped = clamped;
+        T = Tn;
+        last = (int32_t)(j - s + 1);
+        sig = (sig ^ (uint64_t)(j - s)) * 1099511628211ull;
+    }
+    w->T = T;
+    w->margin = margin;
+    w->last = last;
+    w->nclose = nclose;
+    w->sig = sig;
+    return 0;
+}
 
 int orc_render(int W, int H, int tile_w, int tile_h, const double *uv, const double *conic,
                const double *opacity, const double *rgb, const double *depth,
                const uint32_t *vals, const uint32_t *ranges, int n_sel, const int32_t *sel_tiles,
                double *out_rgb, double *out_depth, double *out_alpha, double *out_T,
                int32_t *out_ncontrib, double *out_margin, uint64_t *out_sig,
-               const float *uv_f, const double *conic_f) {
-    const int allow = uv_f && conic_f;
+               const float *uv_f, const double *conic_f, double close_margin, int flip,
+               int32_t *out_nclose) {
     int tiles_x = (W + tile_w - 1) / tile_w;
     int tiles_y = (H + tile_h - 1) / tile_h;
     int nt = sel_tiles ? n_sel : tiles_x * tiles_y;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int it = 0; it < nt; ++it) {
-        int t = sel_tiles ? sel_tiles[it] : it;
-        if (t < 0 || t >= tiles_x * tiles_y) continue;
-        int tx = t % tiles_x, ty = t / tiles_x;
-        uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
-        for (int py = ty * tile_h; py < (ty + 1) * tile_h && py < H; ++py)
-            for (int px = tx * tile_w; px < (tx + 1) * tile_w && px < W; ++px) {
-                double T = 1.0, C[3] = {0, 0, 0}, D = 0, margin = INFINITY;
-                double eT = 0; /* relative allowance of T */
-                int32_t last = 0;
-                uint64_t sig = 1469598103934665603ull; /* FNV-1a of the contributing positions */
-                for (uint32_t j = s; j < e; ++j) {
-                    uint32_t g = vals[j];
-                    double dx = uv[2 * g] - px, dy = uv[2 * g + 1] - py;
-                    double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
-                    double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
-                    double scale = 0.5 * (fabs(A) * dx * dx + fabs(Cc) * dy * dy) + fabs(B * dx * dy);
-                    if (scale > 0) { double mp = fabs(power) / scale; if (mp < margin) margin = mp; }
-                    double da = 0; /* relative allowance of o G and alpha */
-                    if (allow) {
-                        double fx = (double)uv_f[2 * g] - px, fy = (double)uv_f[2 * g + 1] - py;
-                        double Af = conic_f[3 * g], Bf = conic_f[3 * g + 1], Cf = conic_f[3 * g + 2];
-                        double pf = -0.5 * (Af * fx * fx + Cf * fy * fy) - Bf * fx * fy;
-                        double sf = 0.5 * (fabs(Af) * fx * fx + fabs(Cf) * fy * fy) + fabs(Bf * fx * fy);
-                        da = fabs(pf - power) + 16.0 * U32 * (sf + 1.0);
+    walk_in in = {uv, conic, opacity, uv_f, conic_f, close_margin, flip};
+    int err = 0;
+#pragma omp parallel
+    {
+        walk_out w;
+        memset(&w, 0, sizeof w);
+#pragma omp for schedule(dynamic, 1)
+        for (int it = 0; it < nt; ++it) {
+            int t = sel_tiles ? sel_tiles[it] : it;
+            if (t < 0 || t >= tiles_x * tiles_y) continue;
+            int tx = t % tiles_x, ty = t / tiles_x;
+            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+            for (int py = ty * tile_h; py < (ty + 1) * tile_h && py < H; ++py)
+                for (int px = tx * tile_w; px < (tx + 1) * tile_w && px < W; ++px) {
+                    if (walk_pixel(&in, vals, s, e, px, py, &w)) {
+#pragma omp atomic write
+                        err = 1;
+                        continue;
                     }
-                    if (power > 0) continue;
-                    double oG = opacity[g] * exp(power);
-                    double mc = rel_margin(oG, ALPHA_MAX) - da;
-                    if (mc < margin) margin = mc;
-                    double alpha = oG < ALPHA_MAX ? oG : ALPHA_MAX;
-                    double ma = rel_margin(alpha, ALPHA_MIN) - da;
-                    if (ma < margin) margin = ma;
-                    if (alpha < ALPHA_MIN) continue;
-                    double Tn = T * (1.0 - alpha);
-                    if (allow) eT += alpha / (1.0 - alpha) * da + 2.0 * U32;
-                    double mt = rel_margin(Tn, T_MIN) - eT;
-                    if (mt < margin) margin = mt;
-                    if (Tn < T_MIN) break;
-                    for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * alpha * T;
-                    D += depth[g] * alpha * T;
-                    T = Tn;
-                    last = (int32_t)(j - s + 1);
-                    sig = (sig ^ (uint64_t)(j - s)) * 1099511628211ull;
+                    /* Eq. (3), (4): sums of x_i alpha_i T_i; Eq. (5): V = 1 - T */
+                    double C[3] = {0, 0, 0}, D = 0;
+                    for (size_t i = 0; i < w.cnt; ++i) {
+                        const contrib_t *c = &w.lst[i];
+                        double wgt = c->alpha * c->T;
+                        for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * c->g + ch] * wgt;
+                        D += depth[c->g] * wgt;
+                    }
+                    size_t p = (size_t)py * W + px;
+                    if (out_sig) out_sig[p] = w.sig;
+                    for (int ch = 0; ch < 3; ++ch) out_rgb[(size_t)ch * W * H + p] = C[ch];
+                    out_depth[p] = D;
+                    out_alpha[p] = 1.0 - w.T;
+                    out_T[p] = w.T;
+                    out_ncontrib[p] = w.last;
+                    if (out_margin) out_margin[p] = w.margin;
+                    if (out_nclose) out_nclose[p] = w.nclose;
                 }
-                size_t p = (size_t)py * W + px;
-                if (out_sig) out_sig[p] = sig;
-                for (int ch = 0; ch < 3; ++ch) out_rgb[(size_t)ch * W * H + p] = C[ch];
-                out_depth[p] = D;
-                out_alpha[p] = 1.0 - T;
-                out_T[p] = T;
-                out_ncontrib[p] = last;
-                if (out_margin) out_margin[p] = margin;
-            }
+        }
+        free(w.lst);
     }
-    return ORC_OK;
+    return err ? ORC_ERR_MEM : ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -589,25 +716,22 @@ int orc_render(int W, int H, int tile_w, int tile_h, const double *uv, const dou
 /*   dX/dx_i     = w_i                                                       */
 /* then alpha_i = o_i exp(power_i) with power as in Eq. (6).                */
 /* Output per Gaussian (10 doubles): du, dv, dA, dB, dC, dopacity,           */
-/* drgb[3], ddepth.                                                          */
+/* drgb[3], ddepth.  The walk (and its close_margin / flip) is the one of    */
+/* orc_render.                                                               */
 /* ------------------------------------------------------------------------ */
-typedef struct {
-    uint32_t g;
-    double alpha, T, G, dx, dy;
-    int clamped;
-} contrib_t;
-
 int orc_backward_render(int W, int H, int tile_w, int tile_h, int64_t n, const double *uv,
                         const double *conic, const double *opacity, const double *rgb,
                         const double *depth, const uint32_t *vals, const uint32_t *ranges,
                         const double *dL_drgb, const double *dL_ddepth, const double *dL_dalpha,
-                        double *grad2d) {
+                        double *grad2d, const float *uv_f, const double *conic_f,
+                        double close_margin, int flip) {
     int tiles_x = (W + tile_w - 1) / tile_w;
     int tiles_y = (H + tile_h - 1) / tile_h;
     int nt = tiles_x * tiles_y;
     int nthr = orc_num_threads();
     double *acc = (double *)calloc((size_t)nthr * (size_t)n * 10, sizeof(double));
     if (!acc) return ORC_ERR_MEM;
+    walk_in in = {uv, conic, opacity, uv_f, conic_f, close_margin, flip};
     int err = 0;
 #pragma omp parallel
     {
@@ -616,52 +740,38 @@ int orc_backward_render(int W, int H, int tile_w, int tile_h, int64_t n, const d
         tid = omp_get_thread_num();
 #endif
         double *my = acc + (size_t)tid * (size_t)n * 10;
-        size_t cap = 64;
-        contrib_t *lst = (contrib_t *)malloc(sizeof(contrib_t) * cap);
-        double *suf = (double *)malloc(sizeof(double) * 5 * (cap + 1));
-        if (!lst || !suf) {
-#pragma omp atomic write
-            err = 1;
-        }
+        walk_out w;
+        memset(&w, 0, sizeof w);
+        size_t scap = 0;
+        double *suf = NULL;
 #pragma omp for schedule(dynamic, 1)
         for (int t = 0; t < nt; ++t) {
-            if (!lst || !suf) continue;
             int tx = t % tiles_x, ty = t / tiles_x;
             uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
             for (int py = ty * tile_h; py < (ty + 1) * tile_h && py < H; ++py)
                 for (int px = tx * tile_w; px < (tx + 1) * tile_w && px < W; ++px) {
                     size_t p = (size_t)py * W + px;
-                    /* forward pass over the list, recording the contributors */
-                    size_t cnt = 0;
-                    double T = 1.0;
-                    for (uint32_t j = s; j < e; ++j) {
-                        uint32_t g = vals[j];
-                        double dx = uv[2 * g] - px, dy = uv[2 * g + 1] - py;
-                        double A = conic[3 * g], B = conic[3 * g + 1], Cc = conic[3 * g + 2];
-                        double power = -0.5 * (A * dx * dx + Cc * dy * dy) - B * dx * dy;
-                        if (power > 0) continue;
-                        double G = exp(power);
-                        double oG = opacity[g] * G;
-                        double alpha = oG < ALPHA_MAX ? oG : ALPHA_MAX;
-                        if (alpha < ALPHA_MIN) continue;
-                        double Tn = T * (1.0 - alpha);
-                        if (Tn < T_MIN) break;
-                        if (cnt == cap) {
-                            cap *= 2;
-                            contrib_t *nl = (contrib_t *)realloc(lst, sizeof(contrib_t) * cap);
-                            double *ns = (double *)realloc(suf, sizeof(double) * 5 * (cap + 1));
-                            if (!nl || !ns) { err = 1; if (nl) lst = nl; if (ns) suf = ns; break; }
-                            lst = nl; suf = ns;
-                        }
-                        contrib_t *c = &lst[cnt++];
-                        c->g = g; c->alpha = alpha; c->T = T; c->G = G; c->dx = dx; c->dy = dy;
-                        c->clamped = !(oG < ALPHA_MAX);
-                        T = Tn;
+                    if (walk_pixel(&in, vals, s, e, px, py, &w)) {
+#pragma omp atomic write
+                        err = 1;
+                        continue;
                     }
+                    size_t cnt = w.cnt;
+                    if (cnt + 1 > scap) {
+                        double *ns = (double *)realloc(suf, sizeof(double) * 5 * (cnt + 1));
+                        if (!ns) {
+#pragma omp atomic write
+                            err = 1;
+                            continue;
+                        }
+                        suf = ns;
+                        scap = cnt + 1;
+                    }
+                    const contrib_t *lst = w.lst;
                     /* suffix sums of x_k w_k for x in (r, g, b, depth, 1) */
                     for (int q = 0; q < 5; ++q) suf[5 * cnt + q] = 0;
                     for (size_t i = cnt; i-- > 0;) {
-                        contrib_t *c = &lst[i];
+                        const contrib_t *c = &lst[i];
                         double wgt = c->alpha * c->T;
                         suf[5 * i + 0] = suf[5 * (i + 1) + 0] + rgb[3 * c->g + 0] * wgt;
                         suf[5 * i + 1] = suf[5 * (i + 1) + 1] + rgb[3 * c->g + 1] * wgt;
@@ -674,7 +784,7 @@ int orc_backward_render(int W, int H, int tile_w, int tile_h, int64_t n, const d
                     double gd = dL_ddepth ? dL_ddepth[p] : 0.0;
                     double ga = dL_dalpha ? dL_dalpha[p] : 0.0;
                     for (size_t i = 0; i < cnt; ++i) {
-                        contrib_t *c = &lst[i];
+                        const contrib_t *c = &lst[i];
                         uint32_t g = c->g;
                         double wgt = c->alpha * c->T;
                         double inv = 1.0 / (1.0 - c->alpha);
@@ -698,7 +808,7 @@ int orc_backward_render(int W, int H, int tile_w, int tile_h, int64_t n, const d
                     }
                 }
         }
-        free(lst);
+        free(w.lst);
         free(suf);
     }
     for (int64_t i = 0; i < n * 10; ++i) {
@@ -839,7 +949,10 @@ int orc_backward_preprocess(int64_t n, const float *means, const float *log_scal
 /* (Eq. 10, 11, 12).  SSIM: 11x11 Gaussian window (sigma 1.5, normalised),   */
 /* zero padding, C1 = 0.01^2, C2 = 0.03^2, mean over channels and pixels.    */
 /* L_d: mean |D - D_lidar| over pixels with D_lidar > 0 (0 if none).         */
-/* Gradients with sign(0) = 0.                                               */
+/* Gradients with sign(0) = 0.  With flip = 1 an L1 residual within          */
+/* kink_margin (colour) or depth_kink_margin (depth) of zero takes the other */
+/* sign: the subgradient a residual that small may legitimately get when the */
+/* image is known only to that tolerance.                                    */
 /* ------------------------------------------------------------------------ */
 static void ssim_window(double w[11]) {
     double s = 0;
@@ -849,16 +962,21 @@ static void ssim_window(double w[11]) {
 
 static double sgn(double x) { return x > 0 ? 1.0 : (x < 0 ? -1.0 : 0.0); }
 
+static double sgn_flip(double x, double margin, int flip) {
+    return (flip && fabs(x) <= margin) ? -sgn(x) : sgn(x);
+}
+
 int orc_loss(int W, int H, const double *img, const double *gt, const double *depth,
              const double *lidar, double lambda, double lambda_d, double *loss_terms,
-             double *d_img, double *d_depth) {
+             double *d_img, double *d_depth, double kink_margin, double depth_kink_margin,
+             int flip) {
     size_t P = (size_t)W * H;
     double w1[11];
     ssim_window(w1);
     double l1 = 0;
     for (size_t i = 0; i < 3 * P; ++i) {
         l1 += fabs(img[i] - gt[i]);
-        if (d_img) d_img[i] = (1.0 - lambda) * sgn(img[i] - gt[i]) / (3.0 * P);
+        if (d_img) d_img[i] = (1.0 - lambda) * sgn_flip(img[i] - gt[i], kink_margin, flip) / (3.0 * P);
     }
     l1 /= (3.0 * P);
     double ssim_mean = 0;
@@ -925,7 +1043,8 @@ int orc_loss(int W, int H, const double *img, const double *gt, const double *de
         if (d_depth) d_depth[i] = 0;
         if (!(lidar[i] > 0)) continue;
         ld += fabs(depth[i] - lidar[i]);
-        if (d_depth) d_depth[i] = lambda_d * sgn(depth[i] - lidar[i]) / (double)nvalid;
+        if (d_depth)
+            d_depth[i] = lambda_d * sgn_flip(depth[i] - lidar[i], depth_kink_margin, flip) / (double)nvalid;
     }
     if (nvalid) ld /= (double)nvalid;
     double loss = (1.0 - lambda) * l1 + (lambda != 0.0 ? lambda * (1.0 - ssim_mean) : 0.0) + lambda_d * ld;

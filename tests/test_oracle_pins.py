@@ -37,12 +37,17 @@ def sigmoid(x):
 # --------------------------------------------------------------------------
 # a5 closed forms (Eq. 3-6): one and two isotropic Gaussians on the optical axis
 # --------------------------------------------------------------------------
-def test_single_isotropic_gaussian_closed_form():
+@pytest.mark.parametrize("screen", ["f64", "key"])
+def test_single_isotropic_gaussian_closed_form(screen):
+    """With the binary64 projection the image is the closed form to rounding;
+    with the key stage's (binary32 covariance, centre exact here) alpha moves by
+    at most the covariance's binary32 rounding (a few 2^-24 relative) times
+    the exponent, and a pixel that close to the 1/255 cut may go either way."""
     W, H, f = 64, 48, 50.0
     cam = O.Camera(np.eye(3), np.zeros(3), f, f, 32.0, 24.0, W, H)
     z, s, logit, col = 4.0, 0.2, 1.0, np.array([0.9, 0.5, 0.2])
     p = one_gaussian_params([[0, 0, z]], [math.log(s)], [logit], [col])
-    r = O.render_view(p, cam, 0)
+    r = O.render_view(p, cam, 0, screen=screen)
     s_eff = math.exp(float(np.float32(math.log(s))))  # the parameter is a binary32 log-scale
     sig2 = (f * s_eff / z) ** 2 + 0.3
     # radius from the eigenvalues of sig2*I (both equal; discriminant floored at 0.1)
@@ -50,8 +55,10 @@ def test_single_isotropic_gaussian_closed_form():
     assert r["pre"]["radius"][0] == rad
     o = sigmoid(logit)
     yy, xx = np.mgrid[0:H, 0:W]
-    a = o * np.exp(-((xx - 32.0) ** 2 + (yy - 24.0) ** 2) / (2 * sig2))
+    power = -((xx - 32.0) ** 2 + (yy - 24.0) ** 2) / (2 * sig2)
+    a = o * np.exp(power)
     a = np.minimum(a, 0.99)
+    near_cut = np.abs(a * 255 - 1) < 1e-5
     a[a < 1 / 255] = 0
     # only the tiles of the covered rectangle are composited
     x0, x1 = int((32 - rad) / 16), int((32 + rad + 15) / 16)
@@ -59,11 +66,17 @@ def test_single_isotropic_gaussian_closed_form():
     cover = np.zeros((H, W), bool)
     cover[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
     a[~cover] = 0
-    np.testing.assert_allclose(r["alpha"], a, atol=1e-12)
-    np.testing.assert_allclose(r["depth"], z * a, atol=1e-11)
+    if screen == "f64":
+        tol, ok = 1e-12, np.ones((H, W), bool)
+    else:
+        tol, ok = 1e-6 * a * (np.abs(power) + 1) + 1e-15, ~near_cut
+    assert ok.mean() > 0.95
+    assert np.all(np.abs(r["alpha"] - a)[ok] <= tol if np.isscalar(tol) else np.abs(r["alpha"] - a)[ok] <= tol[ok])
+    assert np.all(np.abs(r["depth"] - z * a)[ok] <= 10 * (tol if np.isscalar(tol) else tol[ok]))
     for ch in range(3):
-        np.testing.assert_allclose(r["rgb"][ch], col[ch] * a, atol=1e-12)
-    np.testing.assert_allclose(r["final_T"], 1 - a, atol=1e-12)
+        np.testing.assert_allclose(r["rgb"][ch][ok], (col[ch] * a)[ok],
+                                   atol=1e-12 if screen == "f64" else 1e-6 * 6.5)
+    np.testing.assert_allclose(r["final_T"][ok], (1 - a)[ok], atol=1e-12 if screen == "f64" else 1e-6 * 6.5)
 
 
 def test_two_gaussians_closed_form():
@@ -127,6 +140,79 @@ def test_early_stop_closed_form():
 
 
 # --------------------------------------------------------------------------
+# a5: the other branch of close calls (flip), on closed forms
+# --------------------------------------------------------------------------
+def test_flip_takes_the_other_branch_closed_forms():
+    """A test within ``close_margin`` of its threshold takes the other branch
+    under ``flip``; the result is again the closed form, for that branch."""
+    W = H = 16
+    cam = O.Camera(np.eye(3), np.zeros(3), 20.0, 20.0, 8.0, 8.0, W, H)
+    # (a) the stop: 20 on-axis Gaussians, alpha = 1/2 at the centre pixel; T after
+    # 13 of them, 2^-13, is 22 % above 1e-4: with close_margin 0.3 that test is
+    # close, so the flipped walk stops before the 13th (T = 2^-12)
+    n = 20
+    cols = np.random.default_rng(9).uniform(0.1, 0.9, (n, 3))
+    zs = [2.0 + 0.25 * i for i in range(n)]
+    p = one_gaussian_params([[0, 0, z] for z in zs], [math.log(0.05)] * n, [0.0] * n, cols)
+    r0 = O.render_view(p, cam, 0, screen="f64", close_margin=0.3)
+    r1 = O.render_view(p, cam, 0, screen="f64", close_margin=0.3, flip=True)
+    assert r0["n_contrib"][8, 8] == 13 and r0["n_close"][8, 8] >= 1
+    assert r1["n_contrib"][8, 8] == 12
+    assert r1["final_T"][8, 8] == pytest.approx(2.0 ** -12, rel=1e-14)
+    w = 0.5 * 0.5 ** np.arange(12)
+    np.testing.assert_allclose(r1["rgb"][:, 8, 8], (cols[:12] * w[:, None]).sum(0), rtol=1e-6)
+    np.testing.assert_allclose(r1["depth"][8, 8], (np.array(zs[:12]) * w).sum(), rtol=1e-13)
+    # without flip, close_margin only counts
+    r2 = O.render_view(p, cam, 0, screen="f64")
+    for k in ("rgb", "depth", "alpha", "n_contrib"):
+        assert np.array_equal(r0[k], r2[k])
+    # ... and no close test, no flip
+    r3 = O.render_view(p, cam, 0, screen="f64", flip=True)
+    for k in ("rgb", "depth", "alpha", "n_contrib"):
+        assert np.array_equal(r3[k], r2[k])
+    # the backward over the flipped walk is the backward of the first 12 alone
+    rng = np.random.default_rng(4)
+    d_rgb = np.zeros((3, H, W)); d_rgb[:, 8, 8] = rng.normal(size=3)
+    d_dep = np.zeros((H, W)); d_dep[8, 8] = 0.3
+    d_alp = np.zeros((H, W)); d_alp[8, 8] = -0.7
+    g_flip = O.backward_render(r1["pre"], r1["vals"], r1["ranges"], W, H, d_rgb, d_dep, d_alp,
+                               close_margin=0.3, flip=True)
+    p12 = {k: (v[:12] if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+    r12 = O.render_view(p12, cam, 0, screen="f64")
+    assert r12["n_contrib"][8, 8] == 12
+    g12 = O.backward_render(r12["pre"], r12["vals"], r12["ranges"], W, H, d_rgb, d_dep, d_alp)
+    np.testing.assert_allclose(g_flip[:12], g12, rtol=1e-12, atol=1e-15)
+    assert np.all(g_flip[12:] == 0)
+
+    # (b) the clamp: o = 0.995 at the centre of one Gaussian, 0.5 % above 0.99
+    p = one_gaussian_params([[0, 0, 3.0]], [math.log(0.05)], [math.log(0.995 / 0.005)], [[0.3, 0.6, 0.9]])
+    o = sigmoid(float(p["opacity_logits"][0]))
+    r0 = O.render_view(p, cam, 0, screen="f64", close_margin=0.01)
+    r1 = O.render_view(p, cam, 0, screen="f64", close_margin=0.01, flip=True)
+    assert r0["alpha"][8, 8] == pytest.approx(0.99, rel=1e-14)
+    assert r1["alpha"][8, 8] == pytest.approx(o, rel=1e-14)
+
+    # (c) the 1/255 cut: a wide Gaussian (sigma ~ 6 px); every pixel whose only
+    # close test is its cut shows the closed form alpha when taken, 0 when not
+    W2 = H2 = 48
+    cam2 = O.Camera(np.eye(3), np.zeros(3), 60.0, 60.0, 24.0, 24.0, W2, H2)
+    z, sc, logit = 2.0, 0.2, -1.0
+    p = one_gaussian_params([[0, 0, z]], [math.log(sc)], [logit], [[1.0, 1.0, 1.0]])
+    o = sigmoid(float(p["opacity_logits"][0]))
+    s_eff = math.exp(float(np.float32(math.log(sc))))
+    sig2 = (60.0 * s_eff / z) ** 2 + 0.3
+    yy, xx = np.mgrid[0:H2, 0:W2]
+    a = o * np.exp(-((xx - 24.0) ** 2 + (yy - 24.0) ** 2) / (2 * sig2))
+    r0 = O.render_view(p, cam2, 0, tile=(48, 48), screen="f64", close_margin=0.05)
+    r1 = O.render_view(p, cam2, 0, tile=(48, 48), screen="f64", close_margin=0.05, flip=True)
+    close = r0["n_close"] > 0
+    assert close.sum() >= 8 and np.all(np.abs(a[close] * 255 - 1) <= 0.05)
+    want = np.where(a >= 1 / 255, 0.0, a)  # the other branch of the cut
+    np.testing.assert_allclose(r1["alpha"][close], want[close], rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(r1["alpha"][~close], r0["alpha"][~close])
+
+
+# --------------------------------------------------------------------------
 # a1: EWA covariance against a finite-difference Jacobian of the projection
 # --------------------------------------------------------------------------
 def _quat_R(q):
@@ -149,7 +235,9 @@ def test_projection_covariance_matches_fd_jacobian():
                   quats=rng.normal(size=(n, 4)).astype(np.float32),
                   opacity_logits=np.zeros(n, np.float32), sh=np.zeros((n, 1, 3), np.float32),
                   sh_degree=0)
-    pre = O.preprocess(params, cam)
+    pre = O.preprocess(params, cam, screen="f64")
+    # the key stage's screen-space Gaussian is the same projection in binary32
+    prek = O.preprocess(params, cam, screen="key")
     Rd, td = np.asarray(cam.R, np.float64), np.asarray(cam.t, np.float64)
 
     def proj(p):
@@ -170,6 +258,11 @@ def test_projection_covariance_matches_fd_jacobian():
                                    rtol=1e-6, atol=1e-9)
         np.testing.assert_allclose(pre["uv"][i], proj(pc), rtol=1e-12)
         assert pre["depth"][i] == pytest.approx(pc[2], rel=1e-12)
+        ref = np.array([inv[0, 0], inv[0, 1], inv[1, 1]])
+        assert np.abs(prek["conic"][i] - ref).max() <= 1e-5 * np.abs(ref).max()
+        np.testing.assert_allclose(prek["uv"][i], proj(pc), rtol=1e-6)
+        assert prek["depth"][i] == pytest.approx(pc[2], rel=1e-6)
+        assert prek["uv"][i, 0] == float(prek["uv_f"][i, 0]) and prek["depth"][i] == float(prek["z_f"][i])
 
 
 def test_quaternion_sign_invariance_and_radius_eigen():
@@ -360,6 +453,17 @@ def test_l1_and_depth_terms_closed_form():
     assert d_img[0, 0, 0] == pytest.approx(-1 / 12) and d_img[2, 1, 1] == pytest.approx(1 / 12)
     assert d_img[1, 0, 0] == 0.0  # sign(0) = 0
     np.testing.assert_allclose(d_depth, [[0, -0.25], [0.25, 0]])
+    # residuals within the kink margins take the other sign under flip; the
+    # values do not change
+    x2 = x.copy(); x2[0, 0, 0] = 0.6 + 1e-5
+    d2 = depth.copy(); d2[0, 1] = 2.5 - 2e-4
+    t_a, g_a, gd_a = O.loss(x2, y, d2, lidar, 0.0, 0.5)
+    t_b, g_b, gd_b = O.loss(x2, y, d2, lidar, 0.0, 0.5, kink_margin=1e-4, depth_kink_margin=1e-3, flip=True)
+    np.testing.assert_array_equal(t_a, t_b)
+    assert g_a[0, 0, 0] == pytest.approx(1 / 12) and g_b[0, 0, 0] == pytest.approx(-1 / 12)
+    assert gd_a[0, 1] == pytest.approx(-0.25) and gd_b[0, 1] == pytest.approx(0.25)
+    g_b[0, 0, 0] = g_a[0, 0, 0]; gd_b[0, 1] = gd_a[0, 1]
+    np.testing.assert_array_equal(g_a, g_b); np.testing.assert_array_equal(gd_a, gd_b)
 
 
 def test_loss_gradient_fd():
@@ -433,16 +537,42 @@ def _fd_scene():
     return params, cam, gt, lidar
 
 
-def _loss_of(params, cam, gt, lidar):
-    r = O.render_view(params, cam, 0)
+def _vis_weights(cam):
+    """Seeded weights of a visibility term sum_p w_p V_p (Eq. 5), of the size
+    of the loss's per-pixel image gradients, so that the dL/dV path of the
+    backward carries a share of every gradient comparable to colour and depth."""
+    return np.random.default_rng(13).normal(0, 3e-4, (cam.H, cam.W))
+
+
+def _loss_of(params, cam, gt, lidar, wv):
+    r = O.render_view(params, cam, 0, screen="f64")
     terms, _, _ = O.loss(r["rgb"], gt, r["depth"], lidar, 0.2, 0.1, grads=False)
-    return terms[0], r
+    return terms[0] + float((wv * r["alpha"]).sum()), r
+
+
+def _analytic_grads(params, cam, gt, lidar, wv):
+    """render -> loss + sum w V -> backward, all binary64 (smooth projection)."""
+    r = O.render_view(params, cam, 0, screen="f64")
+    _, d_img, d_dep = O.loss(r["rgb"], gt, r["depth"], lidar, 0.2, 0.1)
+    g2 = O.backward_render(r["pre"], r["vals"], r["ranges"], cam.W, cam.H, d_img, d_dep, wv)
+    return O.backward_preprocess(params, cam, r["pre"], g2), r
 
 
 def test_backward_matches_central_fd():
+    """Central differences (eps 1e-4, binary64) of L + sum_p w_p V_p through the
+    whole render -> loss pipeline against the hand-derived backward, on every
+    parameter of the visible Gaussians (SH rows on 8 of them).  The V term
+    pins the visibility gradient dV/dalpha_i = T_i - (sum of the weights behind
+    i) / (1 - alpha_i) of Eq. (5); without it the check would not see a
+    mistake there."""
     params, cam, gt, lidar = _fd_scene()
-    out, grads = O.train_step(params, [cam], [0], [gt], [lidar], 0.2, 0.1)
-    base = out[0]["render"]
+    wv = _vis_weights(cam)
+    grads, base = _analytic_grads(params, cam, gt, lidar, wv)
+    grads_nov, _ = _analytic_grads(params, cam, gt, lidar, np.zeros_like(wv))
+    # the visibility term moves every parameter's gradient materially
+    for name in ("means", "log_scales", "quats", "opacity_logits"):
+        d = np.linalg.norm(grads[name] - grads_nov[name]) / np.linalg.norm(grads[name])
+        assert d > 0.05, (name, d)
     assert (base["pre"]["tiles"] > 0).sum() > 40
     eps = 1e-4
     names = ["means", "log_scales", "quats", "opacity_logits", "sh"]
@@ -464,8 +594,8 @@ def test_backward_matches_central_fd():
                 ap[gi, k] += np.float32(eps)
                 am[gi, k] -= np.float32(eps)
                 h = float(ap[gi, k]) - float(am[gi, k])
-                lp, rp = _loss_of(pp, cam, gt, lidar)
-                lm, rm = _loss_of(pm, cam, gt, lidar)
+                lp, rp = _loss_of(pp, cam, gt, lidar, wv)
+                lm, rm = _loss_of(pm, cam, gt, lidar, wv)
                 # same tile lists in the same order (the depth bits of the keys may move)
                 same = (np.array_equal(rp["keys"] >> np.uint64(32), rm["keys"] >> np.uint64(32))
                         and np.array_equal(rp["vals"], rm["vals"])
@@ -483,6 +613,7 @@ def test_backward_matches_central_fd():
                 worst = max(worst, err)
                 assert err < 2e-5, (name, gi, k, fd, an)
                 n_checked += 1
+    print(f"  checked {n_checked}, skipped {n_skipped}, worst {worst:.2e}")
     # a perturbation that flips any threshold test anywhere in the image is skipped
     assert n_checked > 900 and n_skipped < 0.1 * (n_checked + n_skipped)
 
@@ -500,18 +631,22 @@ def test_exp_key_is_binary64_exp_rounded_once():
 def test_render_margin_allowance_covers_binary32_evaluation():
     """The render margin's binary32 allowance: (1) the conic of the binary32
     covariance is the float64 conic up to binary32 rounding (amplified where
-    the projection cancels a 3D covariance elongated along the ray); (2) the allowance
-    only lowers margins; (3) an independent binary32 evaluation of every
-    examined alpha (numpy float32: the key stage's centre, that conic rounded to
-    binary32, float32 exp) takes the 1/255 and 0.99 decisions the other way
-    only at pixels whose margin is at most 0."""
+    the projection cancels a 3D covariance elongated along the ray); (2) with
+    the binary64 projection the deviation of the binary32 inputs is charged
+    too, which only lowers margins; (3) an independent binary32 evaluation of
+    every examined alpha (numpy float32: the key stage's centre, that conic
+    rounded to binary32, float32 exp) takes the 1/255 and 0.99 decisions the
+    other way only at pixels whose margin is at most 0."""
     params, phase = S.lidar_scene(300_000)
     cam = O.level_camera(cam_of(S.trajectory_cameras(1, phase=phase)[0]), 1)
     pre = O.preprocess(params, cam)
+    pre64 = O.preprocess(params, cam, screen="f64")
     vis = pre["radius"] > 0
-    cf, c64 = pre["conic_f"][vis], pre["conic"][vis]
+    cf, c64 = pre["conic_f"][vis], pre64["conic"][vis]
     dev = np.abs(cf - c64).max(axis=1) / np.abs(c64).max(axis=1)
     assert np.median(dev) < 1e-6 and dev.max() < 1e-4
+    # the values composited are the key stage's
+    assert np.array_equal(pre["conic"], pre["conic_f"]) and np.array_equal(pre["uv"], pre["uv_f"].astype(np.float64))
 
     keys, vals = O.build_keys(pre)
     ranges = O.tile_ranges(keys, pre["tiles_x"] * pre["tiles_y"])
@@ -520,8 +655,15 @@ def test_render_margin_allowance_covers_binary32_evaluation():
     plain = dict(pre)
     del plain["conic_f"]
     img0 = O.render(plain, vals, ranges, cam.W, cam.H, sel_tiles=sel)
-    assert np.all(img["margin"] <= img0["margin"])
+    # in the key stage's values the binary32 inputs deviate by nothing
+    assert np.array_equal(img["margin"], img0["margin"])
     assert np.array_equal(img["rgb"], img0["rgb"]) and np.array_equal(img["n_contrib"], img0["n_contrib"])
+    img64 = O.render(pre64, vals, ranges, cam.W, cam.H, sel_tiles=sel)
+    plain64 = dict(pre64)
+    del plain64["conic_f"]
+    img64p = O.render(plain64, vals, ranges, cam.W, cam.H, sel_tiles=sel)
+    fin = np.isfinite(img64p["margin"])
+    assert np.all(img64["margin"] <= img64p["margin"]) and (img64["margin"] < img64p["margin"])[fin].mean() > 0.5
 
     f = np.float32
     uvf = pre["uv_f"]
