@@ -752,7 +752,18 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
                                s_acc[8][tid]};
         const float d_mean[3] = {s_acc[0][tid], s_acc[1][tid], s_acc[2][tid]};
         const float d_op = s_acc[9][tid];
-        // Sigma = M M^T with M = R diag(s): dM = 2 dSigma_sym M
+        // dL/dSigma as a symmetric matrix G, seen in the Gaussian's own frame:
+        // Gb = R^T G R.  Sigma = R diag(s^2) R^T (Eq. 2), so
+        //   dL/d log s_j = 2 s_j^2 Gb_jj,
+        // and a rotation dR = [w]x R changes L by -2 c . w, where [c]x is the
+        // commutator Sigma G - G Sigma = R [diag(s^2), Gb] R^T, whose entries
+        // in the own frame are (s_i^2 - s_j^2) Gb_ij.  The chain rule through
+        // R(q) and the normalisation gives the same gradient, but forms it as
+        // a large radial part minus its projection; for a nearly isotropic
+        // Gaussian that difference cancels most digits of a binary32 result.
+        // Here the small factors s_i^2 - s_j^2 are formed directly (exactly
+        // for close scales), so each component keeps binary32 accuracy
+        // relative to the rotation gradient itself.
         float dS[3][3];
         dS[0][0] = dSig[0];
         dS[1][1] = dSig[3];
@@ -760,28 +771,36 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         dS[0][1] = dS[1][0] = 0.5f * dSig[1];
         dS[0][2] = dS[2][0] = 0.5f * dSig[2];
         dS[1][2] = dS[2][1] = 0.5f * dSig[4];
-        float d_ls[3], dR[9];
+        float GR[3][3]; // G R
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            float dsj = 0.f;
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float dMij = 2.f * (dS[i][0] * M[j] + dS[i][1] * M[3 + j] + dS[i][2] * M[6 + j]);
-                dsj += dMij * r[3 * i + j];
-                dR[3 * i + j] = dMij * s[j];
-            }
-            d_ls[j] = dsj * s[j];
-        }
-        float dq[4];
-        dq[0] = 2.f * (-qz * dR[1] + qy * dR[2] + qz * dR[3] - qx * dR[5] - qy * dR[6] + qx * dR[7]);
-        dq[1] = 2.f * (qy * dR[1] + qz * dR[2] + qy * dR[3] - 2.f * qx * dR[4] - qw * dR[5] + qz * dR[6] +
-                       qw * dR[7] - 2.f * qx * dR[8]);
-        dq[2] = 2.f * (-2.f * qy * dR[0] + qx * dR[1] + qw * dR[2] + qx * dR[3] + qz * dR[5] - qw * dR[6] +
-                       qz * dR[7] - 2.f * qy * dR[8]);
-        dq[3] = 2.f * (-2.f * qz * dR[0] - qw * dR[1] + qx * dR[2] + qw * dR[3] - 2.f * qz * dR[4] +
-                       qy * dR[5] + qx * dR[6] + qy * dR[7]);
-        const float qdot = dq[0] * qw + dq[1] * qx + dq[2] * qy + dq[3] * qz;
-        const float qn[4] = {qw, qx, qy, qz};
+            for (int j = 0; j < 3; ++j)
+                GR[i][j] = dS[i][0] * r[j] + dS[i][1] * r[3 + j] + dS[i][2] * r[6 + j];
+        float Gb[3][3]; // R^T G R
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                Gb[i][j] = r[i] * GR[0][j] + r[3 + i] * GR[1][j] + r[6 + i] * GR[2][j];
+        float d_ls[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d_ls[j] = 2.f * s[j] * s[j] * Gb[j][j];
+        // own-frame c, then world frame c = R c_own
+        const float c0 = (s[2] - s[1]) * (s[2] + s[1]) * Gb[2][1];
+        const float c1 = (s[0] - s[2]) * (s[0] + s[2]) * Gb[0][2];
+        const float c2 = (s[1] - s[0]) * (s[1] + s[0]) * Gb[1][0];
+        const float cw0 = r[0] * c0 + r[1] * c1 + r[2] * c2;
+        const float cw1 = r[3] * c0 + r[4] * c1 + r[5] * c2;
+        const float cw2 = r[6] * c0 + r[7] * c1 + r[8] * c2;
+        // unit quaternion (w, v): a world rotation w moves it by (0, w) (x) q / 2,
+        // so the gradient is -4 [-v . c ; w c - v x c], divided by |q| for the
+        // unnormalised parameter
+        float dqt[4];
+        dqt[0] = -(qx * cw0 + qy * cw1 + qz * cw2);
+        dqt[1] = qw * cw0 - (qy * cw2 - qz * cw1);
+        dqt[2] = qw * cw1 - (qz * cw0 - qx * cw2);
+        dqt[3] = qw * cw2 - (qx * cw1 - qy * cw0);
         const float o = 1.f / (1.f + expf(-P.opacity_logits[g]));
         // the compositing backward accumulates o dL/do (its exponent holds log2 o)
         const float d_logit = d_op * (1.f - o);
@@ -792,7 +811,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
                 G.d_log_scales[3 * g + k] = d_ls[k];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] = (dq[k] - qn[k] * qdot) * qi;
+            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] = -4.f * dqt[k] * qi;
             G.d_opacity_logits[g] = d_logit;
         } else {
 #pragma unroll
@@ -801,7 +820,7 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
                 G.d_log_scales[3 * g + k] += d_ls[k];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] += (dq[k] - qn[k] * qdot) * qi;
+            for (int k = 0; k < 4; ++k) G.d_quats[4 * g + k] += -4.f * dqt[k] * qi;
             G.d_opacity_logits[g] += d_logit;
         }
     }
@@ -854,7 +873,7 @@ const ExpKeyTable &exp_key_table() {
 void launch_exp_key(const float *x, float *y, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
     exp_key_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, y, n, exp_key_table());
 }
 
