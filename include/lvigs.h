@@ -215,8 +215,12 @@ lvigs_status lvigs_loss(lvigs_ctx *ctx, int width, int height, const float *rgb,
  * errors of lvigs_loss; LVIGS_ERR_CUDA when a CUDA call fails.
  *
  * Set-up: the first call on a device looks up the device address of the
- * scratch array (which may load the library's module onto that device), so
- * make that first call before any stream capture begins.
+ * scratch array (which may create the device's primary context and load the
+ * library's module onto it), so make that first call before any stream
+ * capture begins.  The address is kept with the id of the context it came
+ * from; after a device reset (cudaDeviceReset, or the primary context released
+ * and created again) the next call looks it up again in the new context, so
+ * that call is a first call too.
  *
  * Every call on a device shares the one array, and it keeps what the last
  * call left (no call depends on it: each writes everything it reads).  Calls

@@ -14,7 +14,8 @@
 //
 // The kernels are those of lvigs_loss (loss.cu); only where their scratch
 // lives differs, so results are identical for identical inputs.
-#include <atomic>
+#include <cuda.h>
+
 #include <mutex>
 
 #include "lvigs.h"
@@ -35,27 +36,64 @@ constexpr int kMaxDevices = 64;
 // (each call writes every element it later reads).
 static __device__ __align__(256) unsigned char lvigs_loss_scratch[kScratchBytes];
 
-// Device address of lvigs_loss_scratch per device ordinal, looked up once.
-std::atomic<void *> g_scratch_addr[kMaxDevices];
+// Device address of lvigs_loss_scratch per device ordinal, with the id of the
+// context it was looked up in.  A device reset (or the primary context being
+// released and created again) loads the module afresh, possibly elsewhere, so
+// the address is valid only while the context that gave it is current.
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    void *addr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 std::mutex g_setup_mu;
+
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points (the
+// library links the runtime only).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+lvigs_status current_context_id(unsigned long long *id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return LVIGS_ERR_CUDA;
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return LVIGS_ERR_CUDA;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return LVIGS_ERR_CUDA;
+    return LVIGS_OK;
+}
 
 // With the caller's device current: the device address of the scratch array.
 // Host code may not use the symbol itself (it names a host-side shadow, not
 // device memory), so the address comes from cudaGetSymbolAddress, once per
-// device.  That first lookup may load the module onto the device.
+// device and context.  That first lookup may create the device's primary
+// context and load the module onto it.
 lvigs_status scratch_address(void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LVIGS_ERR_CUDA;
-    void *p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        std::lock_guard<std::mutex> lock(g_setup_mu);
-        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
-        if (!p) {
-            const cudaError_t e = cudaGetSymbolAddress(&p, lvigs_loss_scratch);
-            if (e != cudaSuccess || !p) return LVIGS_ERR_CUDA;
-            g_scratch_addr[dev].store(p, std::memory_order_release);
-        }
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    ScratchSlot &slot = g_scratch[dev];
+    unsigned long long id = 0;
+    // no current context yet: the lookup below creates it
+    if (current_context_id(&id) == LVIGS_OK && slot.addr && slot.ctx_id == id) {
+        *out = slot.addr;
+        return LVIGS_OK;
     }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, lvigs_loss_scratch);
+    if (e != cudaSuccess || !p) return LVIGS_ERR_CUDA;
+    const lvigs_status st = current_context_id(&id);
+    if (st != LVIGS_OK) return st;
+    slot.addr = p;
+    slot.ctx_id = id;
     *out = p;
     return LVIGS_OK;
 }
