@@ -182,17 +182,38 @@ def recorded_traffic(phase):
     return None
 
 
+# FP32 operations charged per visited (pixel, Gaussian) pair: 20 for the
+# forward compositing and 60 for the backward (each plus one exponential), the
+# per-pair work of Eq. (3)-(6) and of its reverse traversal.  Visited pairs
+# are counted as the sum over pixels of the last contributor's list position:
+# every pair is charged in full, although most pairs of the coarse levels fail
+# the 1/255 test after a few operations, so the achieved rate is an upper bound.
+FLOP_PER_PAIR = {"composite_fwd": 20.0, "composite_bwd": 60.0}
+
+
 def alu_flops(n_contrib_sum):
-    # FP32 operations per (pixel, Gaussian) evaluation, counted in the kernel
-    # source (an FMA counts 2): forward 20 (offset, quadratic form 7, exp 2,
-    # alpha 2, transmittance 2, colour/depth 5, weight 1), backward 50 (the
-    # forward's 13 to alpha, the transmittance division 2, weight 1, the
-    # upstream dot product 8, dL/dalpha 2, its running sum 3, colour/depth
-    # partials 8, the five moments of dL/dpower 11, dL/dopacity 2).
-    # Evaluations are counted as the sum over pixels of the last contributor's
-    # list position, an upper bound (it includes list entries the 8x8-block
-    # culling skips), so the achieved rate is an upper bound too.
-    return {"composite_fwd": 20.0 * n_contrib_sum, "composite_bwd": 50.0 * n_contrib_sum}
+    return {k: v * n_contrib_sum for k, v in FLOP_PER_PAIR.items()}
+
+
+def roofline_table(phase_ms, ab, flops, ms_step, hbm_peak, alu_peak):
+    """Per phase: device ms (eager step with events per phase), algorithmic
+    bytes and the fraction of the HBM peak they reach; for the compositing
+    phases also the FP32 rate against the ALU peak.  Plus the whole step:
+    every phase's algorithmic bytes over the graph-replayed step time."""
+    phases = {}
+    for k, ms in phase_ms.items():
+        row = {"ms": round(ms, 4)}
+        if ab.get(k):
+            gbs = ab[k] / (ms / 1e3) / 1e9
+            row.update(bytes=int(ab[k]), gbs=round(gbs, 1), hbm_frac=round(gbs / hbm_peak, 3))
+        if k in flops:
+            tf = flops[k] / (ms / 1e3) / 1e12
+            row.update(tflops=round(tf, 2), alu_frac=round(tf / alu_peak, 3))
+        phases[k] = row
+    total = float(sum(v for k, v in ab.items() if k in phase_ms))
+    gbs = total / (ms_step / 1e3) / 1e9
+    step = {"bytes": int(total), "ms": round(ms_step, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 4)}
+    return step, phases
 
 
 def run_ours(args):
@@ -363,20 +384,24 @@ def run_ours(args):
     ab = algorithmic_bytes(N, V, K, n_vis, M, P_px, M, pyr_px)
     flops = alu_flops(nc_sum)
     hbm_peak, sm_max, peak_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # FP32 FMA pipe: SMs x 128 lanes x 2 FLOP x max SM clock
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
     dominant = max(phase_ms, key=lambda k: phase_ms[k])
     t_dom = phase_ms[dominant] / 1e3
     if dominant in flops:
-        # FP32 FMA pipe: 152 SMs x 128 lanes x 2 FLOP x max SM clock
-        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": flops[dominant] / t_dom / 1e12,
                 "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": recorded_traffic(dominant),
-                "peak_source": "152 SM x 128 FP32 lanes x 2 x sm_max_mhz",
+                "peak_source": f"{n_sm} SM x 128 FP32 lanes x 2 x sm_max_mhz",
+                "flop_per_pair": FLOP_PER_PAIR[dominant],
                 "hbm_achieved_gbs": ab[dominant] / t_dom / 1e9}
     else:
         ach = ab[dominant] / t_dom / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": recorded_traffic(dominant), "peak_source": peak_kind}
+    roof["step"], roof["phases"] = roofline_table(phase_ms, ab, flops, ms_batched, hbm_peak, alu_peak)
+    roof["step"]["peak_source"] = peak_kind
 
     steps_per_s = 1000.0 / ms_batched
     value = job_throughput(world, ms_batched)

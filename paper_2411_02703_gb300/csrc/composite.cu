@@ -954,9 +954,8 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
 
 template <typename K>
 unsigned persistent_grid(K kernel, uint64_t max_items) {
-    int dev = 0, sms = 152, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sm_count();
+    int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerCta * 32, 0);
     if (per_sm < 1) per_sm = 1;
     const uint64_t want = (uint64_t)sms * per_sm;
@@ -1032,14 +1031,14 @@ void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t 
                          cudaStream_t s) {
     if (n_tiles == 0) return;
     int blocks = (int)((n_tiles + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     chunk_count_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, (uint32_t)L, n_chunks, n_slots);
 }
 
 void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s) {
     if (n_tiles == 0) return;
     int blocks = (int)((n_tiles + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     chunk_pairs_kernel<<<blocks, 256, 0, s>>>(cp.n_chunks, cp.chunk_base, cp.part_base, n_tiles,
                                               (uint32_t *)cp.pair_tile, cp.pair_cap, cp.slot_cap, status);
 }
@@ -1047,7 +1046,7 @@ void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status,
 void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s) {
     if (cp.pair_cap == 0) return;
     int blocks = (int)((cp.pair_cap + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     pair_keys_kernel<<<blocks, 256, 0, s>>>(cp.pair_tile, cp.chunk_base, cp.n_pairs, cp.pair_cap, n_tiles, keys, vals);
 }
 
@@ -1055,7 +1054,7 @@ void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan
                           uint32_t *keys, uint32_t *vals, cudaStream_t s) {
     if (cp.pair_cap == 0) return;
     uint64_t blocks = ((uint64_t)cp.pair_cap * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
     if (vs.tile_w == 16 && vs.tile_h == 16)
         bwd_pair_keys_kernel<16, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
     else if (vs.tile_w == 8 && vs.tile_h == 8)

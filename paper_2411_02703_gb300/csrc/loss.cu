@@ -497,7 +497,7 @@ void launch_pyramid_down(int W, int H, const float *rgb, const float *depth, flo
     const int n = (W / 2) * (H / 2);
     if (n <= 0) return;
     int blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     pyramid_down_kernel<<<blocks, 256, 0, s>>>(W, H, rgb, depth, rgb_out, depth_out);
 }
 
@@ -505,7 +505,7 @@ void launch_pyramid_views(const PyrViews &pv, int level, cudaStream_t s) {
     const uint32_t total = pv.n > 0 ? pv.base[pv.n] : 0;
     if (total == 0) return;
     int blocks = (int)((total + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
     switch (level) {
     case 1: pyramid_views_kernel<1><<<blocks, 256, 0, s>>>(pv); break;
     case 2: pyramid_views_kernel<2><<<blocks, 256, 0, s>>>(pv); break;

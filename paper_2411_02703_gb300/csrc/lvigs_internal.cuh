@@ -125,6 +125,26 @@ inline bool kernel_writable(const void *p) {
            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged || pa.type == cudaMemoryTypeHost);
 }
 
+// Streaming multiprocessors of the current device (queried once per device):
+// grid-stride kernels cap their grids at a multiple of it.
+inline int device_sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
 // Kernel launchers (defined in the .cu files, called from the host API).
 namespace lvigs {
 

@@ -303,7 +303,8 @@ __global__ void compact_rows_kernel(const float *__restrict__ src, float *__rest
     }
 }
 
-int blocks_for(int64_t n, int threads, int cap = 152 * 8) {
+int blocks_for(int64_t n, int threads, int per_sm = 8) {
+    const int64_t cap = (int64_t)device_sm_count() * per_sm;
     int64_t b = (n + threads - 1) / threads;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
@@ -314,7 +315,7 @@ int blocks_for(int64_t n, int threads, int cap = 152 * 8) {
 
 void launch_adam(const AdamArgs &A, cudaStream_t s) {
     if (A.unit_base[kAdamSegs] == 0) return;
-    adam_kernel<<<blocks_for(A.unit_base[kAdamSegs], 256, 152 * 16), 256, 0, s>>>(A);
+    adam_kernel<<<blocks_for(A.unit_base[kAdamSegs], 256, 16), 256, 0, s>>>(A);
 }
 
 void launch_point_filter(const float *pts, int64_t k, const PointCamera &C, const float *alpha, float tau, int literal,
@@ -350,7 +351,7 @@ void launch_cell_keys(const float *pts, int64_t k, const KnnGrid &G, uint32_t *k
 void launch_knn(const float *pts, int64_t k, const KnnGrid &G, const uint2 *cells, const uint32_t *order,
                 float min_dist2, float *log_scales_out, cudaStream_t s) {
     if (k <= 0) return;
-    knn_kernel<<<blocks_for(k, 128, 152 * 16), 128, 0, s>>>(pts, k, G, cells, order, min_dist2, log_scales_out);
+    knn_kernel<<<blocks_for(k, 128, 16), 128, 0, s>>>(pts, k, G, cells, order, min_dist2, log_scales_out);
 }
 
 void launch_init_rows(const float *pts, const float *col, const float *log_s, int64_t k, int64_t n0,
@@ -370,7 +371,7 @@ void launch_prune_flags(const float *logits, int64_t n, float thr, uint32_t *kee
 void launch_compact_rows(const float *src, float *dst, int64_t n, int w, const uint32_t *keep, const uint32_t *offs,
                          cudaStream_t s) {
     if (n <= 0) return;
-    compact_rows_kernel<<<blocks_for(n * w, 256, 152 * 16), 256, 0, s>>>(src, dst, n, w, keep, offs);
+    compact_rows_kernel<<<blocks_for(n * w, 256, 16), 256, 0, s>>>(src, dst, n, w, keep, offs);
 }
 
 } // namespace lvigs

@@ -529,7 +529,7 @@ int rs_grid(int64_t n_max) {
 
 int grid_stride_blocks(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
-    const int64_t cap = 152 * 16;
+    const int64_t cap = device_sm_count() * 16;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
