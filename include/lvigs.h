@@ -171,6 +171,18 @@ lvigs_status lvigs_level_size(const lvigs_camera *cam, int level, int *width, in
 lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam,
                           int level, const lvigs_image_out *out, int *view_slot, void *stream);
 
+/* lvigs_render without the wait: the instance lists are sized from the
+ * largest lvigs_render (or earlier no-wait render) of this context instead of
+ * the device's count, so the call only enqueues work.  Same arguments,
+ * results and slot handle as lvigs_render.  If the view has more (tile,
+ * Gaussian) instances than that capacity, the lists are cut at the capacity
+ * (the images then miss the dropped instances) and LVIGS_ERR_CAPACITY is
+ * latched for lvigs_sync_status: render that view once with lvigs_render,
+ * which grows the capacity, and repeat.  A context that has rendered nothing
+ * yet waits once, like lvigs_render. */
+lvigs_status lvigs_render_async(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam,
+                                int level, const lvigs_image_out *out, int *view_slot, void *stream);
+
 /* Gradients of a loss with respect to the Gaussian parameters, given the
  * gradients of that loss with respect to the images of `view_slot`
  * (dL_dalpha may be NULL).  Reverse traversal of each pixel's list with the

@@ -92,6 +92,8 @@ SIGNATURES = {
     "lvigs_level_size": (_I, [ctypes.POINTER(Camera), _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lvigs_render": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _I, ctypes.POINTER(ImageOut),
                           ctypes.POINTER(_I), _P]),
+    "lvigs_render_async": (_I, [_P, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _I,
+                                ctypes.POINTER(ImageOut), ctypes.POINTER(_I), _P]),
     "lvigs_backward": (_I, [_P, _I, _P, _P, _P, ctypes.POINTER(Grads), _P]),
     "lvigs_loss": (_I, [_P, _I, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),
     "lvigs_loss_noalloc": (_I, [_I, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]),

@@ -116,8 +116,12 @@ class Context:
         L.check(code, where, self._h)
 
     # -- plain path --------------------------------------------------------
-    def render(self, params, cam, level=0, sh_degree=None):
-        """Forward render (a1-a5).  Returns (rgb [3,H,W], depth [H,W], alpha [H,W], slot)."""
+    def render(self, params, cam, level=0, sh_degree=None, wait=True):
+        """Forward render (a1-a5).  Returns (rgb [3,H,W], depth [H,W], alpha [H,W], slot).
+
+        wait=False calls lvigs_render_async: no wait on the stream, the
+        instance lists sized from this context's earlier renders (an overflow
+        is reported by sync_status)."""
         g = gaussians_struct(params, sh_degree)
         c = camera_struct(cam)
         W, H = level_size(cam, level)
@@ -127,8 +131,9 @@ class Context:
         alpha = torch.empty((H, W), device=dev, dtype=torch.float32)
         out = L.ImageOut(rgb.data_ptr(), depth.data_ptr(), alpha.data_ptr())
         slot = ctypes.c_int()
-        self._chk(self._lib.lvigs_render(self._h, ctypes.byref(g), ctypes.byref(c), int(level), ctypes.byref(out),
-                                         ctypes.byref(slot), _stream()), "lvigs_render")
+        fn = self._lib.lvigs_render if wait else self._lib.lvigs_render_async
+        self._chk(fn(self._h, ctypes.byref(g), ctypes.byref(c), int(level), ctypes.byref(out), ctypes.byref(slot),
+                     _stream()), "lvigs_render" if wait else "lvigs_render_async")
         return rgb, depth, alpha, slot.value
 
     def backward(self, slot, params, d_rgb, d_depth=None, d_alpha=None, grads=None, accumulate=False):

@@ -26,6 +26,8 @@ struct DevBuf {
 
 // Tile lists longer than this are composited by several warps in parallel.
 constexpr int kChunkLen = 1024;
+// Pinned staging copies of the view descriptors.
+constexpr int kVsRing = 8;
 
 struct RenderState {
     DevBuf recs, tiles, zbits, rects;
@@ -94,13 +96,21 @@ struct lvigs_ctx {
     DevBuf img_rgb, img_depth, img_alpha, d_rgb, d_depth;
     double *host_losses = nullptr;       // pinned [kMaxViews * 4]
     uint32_t *host_batch_counters = nullptr; // pinned [4]
-    ViewSet *vs_staging = nullptr;       // pinned
-    cudaEvent_t vs_event = nullptr, step_event = nullptr;
+    // pinned staging copies of the view descriptors, used in turn: an upload
+    // waits only for the one kVsRing uploads earlier
+    ViewSet *vs_staging = nullptr;       // pinned [kVsRing]
+    cudaEvent_t vs_event[kVsRing] = {};
+    int vs_next = 0;
+    cudaEvent_t step_event = nullptr;
+    // instance capacity of the largest plain render sized so far (the size a
+    // render that does not wait starts from)
+    int64_t render_m_cap = 0;
     bool step_pending = false;
     cudaStream_t cap_stream = nullptr;
     // one graph for steps with their own targets, one per staging slot
     cudaGraphExec_t graph_exec[1 + LVIGS_STAGE_SLOTS] = {};
     BatchKey graph_key[1 + LVIGS_STAGE_SLOTS];
+    BatchKey sized_shape; // the step shape the instance capacity was last sized for
     bool graph_ok[1 + LVIGS_STAGE_SLOTS] = {};
     int kernels_per_step = 0;
     // targets staged by lvigs_stage_targets: per slot the buffers, whether the
@@ -443,11 +453,13 @@ ChunkPlan backward_plan(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
 
 lvigs_status upload_viewset(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
     LV_TRY(ensure(ctx, st.vs_dev, sizeof(ViewSet)));
-    // the pinned staging copy is reused once the previous upload has landed
-    LV_CUDA(cudaEventSynchronize(ctx->vs_event));
-    std::memcpy(ctx->vs_staging, &st.vs, sizeof(ViewSet));
-    LV_CUDA(cudaMemcpyAsync(st.vs_dev.p, ctx->vs_staging, sizeof(ViewSet), cudaMemcpyHostToDevice, s));
-    LV_CUDA(cudaEventRecord(ctx->vs_event, s));
+    // a pinned staging copy is reused once its previous upload has landed
+    const int k = ctx->vs_next;
+    ctx->vs_next = (k + 1) % kVsRing;
+    LV_CUDA(cudaEventSynchronize(ctx->vs_event[k]));
+    std::memcpy(ctx->vs_staging + k, &st.vs, sizeof(ViewSet));
+    LV_CUDA(cudaMemcpyAsync(st.vs_dev.p, ctx->vs_staging + k, sizeof(ViewSet), cudaMemcpyHostToDevice, s));
+    LV_CUDA(cudaEventRecord(ctx->vs_event[k], s));
     return LVIGS_OK;
 }
 
@@ -497,8 +509,9 @@ lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_status, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_losses, kMaxViews * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_batch_counters, 4 * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->vs_staging, sizeof(ViewSet));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->vs_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->vs_staging, kVsRing * sizeof(ViewSet));
+    for (int k = 0; k < kVsRing && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&ctx->vs_event[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->step_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
     for (int k = 0; k < LVIGS_STAGE_SLOTS && e == cudaSuccess; ++k) {
@@ -558,7 +571,8 @@ void lvigs_destroy(lvigs_ctx *ctx) {
         cudaEventDestroy(pe.second.second);
     }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->vs_event) cudaEventDestroy(ctx->vs_event);
+    for (cudaEvent_t ev : ctx->vs_event)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->step_event) cudaEventDestroy(ctx->step_event);
     if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
     if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -575,8 +589,14 @@ lvigs_status lvigs_level_size(const lvigs_camera *cam, int level, int *width, in
     return LVIGS_OK;
 }
 
-lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam, int level,
-                          const lvigs_image_out *out, int *view_slot, void *stream) {
+} // extern "C"
+
+namespace {
+
+// lvigs_render (wait: size the instance lists from the device's count) and
+// lvigs_render_async (no wait: size them from the context's earlier renders).
+lvigs_status render_view(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam, int level,
+                         const lvigs_image_out *out, int *view_slot, void *stream, bool wait) {
     if (!ctx) return LVIGS_ERR_INVALID_ARG;
     LV_TRY(check_gauss(ctx, g));
     LV_TRY(check_camera(ctx, cam, level));
@@ -609,7 +629,10 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     LV_TRY(upload_viewset(ctx, st, s));
     LV_TRY(ensure(ctx, st.final_T, (size_t)st.vs.total_pixels * 4));
     LV_TRY(ensure(ctx, st.n_contrib, (size_t)st.vs.total_pixels * 4));
-    LV_TRY(build_lists(ctx, st, s, true, 1.0));
+    if (!wait && st.m_cap < ctx->render_m_cap) st.m_cap = ctx->render_m_cap;
+    const bool eager = wait || st.m_cap == 0;
+    LV_TRY(build_lists(ctx, st, s, eager, 1.0));
+    if (eager && st.m_cap > ctx->render_m_cap) ctx->render_m_cap = st.m_cap;
     ViewImages im{};
     im.rgb[0] = out->rgb;
     im.depth[0] = out->depth;
@@ -625,6 +648,20 @@ lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     st.generation = (st.generation + 1) & 0x7ffff;
     *view_slot = (int)((st.generation << 12) | (uint32_t)idx);
     return LVIGS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+lvigs_status lvigs_render(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam, int level,
+                          const lvigs_image_out *out, int *view_slot, void *stream) {
+    return render_view(ctx, g, cam, level, out, view_slot, stream, true);
+}
+
+lvigs_status lvigs_render_async(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_camera *cam, int level,
+                                const lvigs_image_out *out, int *view_slot, void *stream) {
+    return render_view(ctx, g, cam, level, out, view_slot, stream, false);
 }
 
 lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb, const float *dL_ddepth,
@@ -953,6 +990,21 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     return LVIGS_OK;
 }
 
+// What the instance count mostly depends on besides the poses: the Gaussian
+// count and each view's size and level.  A step with a shape the capacity was
+// not sized for runs eagerly (it waits once to size the lists) before a graph
+// of that shape is captured.
+BatchKey shape_key(const lvigs_gaussians *g, const lvigs_batch *b) {
+    BatchKey k;
+    k.k.push_back((uint64_t)g->n);
+    k.k.push_back((uint64_t)b->n_views);
+    for (int v = 0; v < b->n_views; ++v) {
+        k.k.push_back((uint64_t)b->cameras[v].width << 32 | (uint32_t)b->cameras[v].height);
+        k.k.push_back((uint64_t)b->levels[v]);
+    }
+    return k;
+}
+
 BatchKey make_key(const lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_batch *b, const lvigs_grads *gr) {
     BatchKey k;
     auto add = [&](uint64_t x) { k.k.push_back(x); };
@@ -1083,9 +1135,11 @@ extern "C" lvigs_status lvigs_train_step_batched(lvigs_ctx *ctx, const lvigs_gau
     BatchKey key = make_key(ctx, g, b, gr);
     const int gi = staged ? 1 + b->staged_slot : 0; // which cached graph
     if (staged) LV_CUDA(cudaStreamWaitEvent(s, ctx->stg_ready[b->staged_slot], 0));
-    if (!use_graph || grow || st.m_cap == 0) {
+    const BatchKey shape = shape_key(g, b);
+    if (!use_graph || grow || st.m_cap == 0 || !(shape == ctx->sized_shape)) {
         // eager step: sizes the instance capacity (waits once on the stream)
         LV_TRY(batched_body(ctx, g, b, gr, s, true));
+        ctx->sized_shape = shape;
     } else {
         if (!ctx->graph_ok[gi] || !(key == ctx->graph_key[gi])) {
             if (ctx->graph_exec[gi]) {

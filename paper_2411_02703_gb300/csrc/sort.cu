@@ -438,9 +438,12 @@ emit_kernel(const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ sorted
             base = vsp->v[vi].tile_base;
             txn = (uint32_t)vsp->v[vi].tiles_x;
             pos0 = offsets[j];
-            if (pos0 + cnt > m_cap) { // the suffix of items past the capacity is dropped
+            // instances past the capacity are dropped: the item that straddles it
+            // keeps its first ones, so that every position below min(M, m_cap),
+            // the count the sort and ranges read, is written by this launch
+            if (pos0 + cnt > m_cap) {
                 atomicOr(status, kStatusCapacity);
-                cnt = 0;
+                cnt = pos0 < m_cap ? (uint32_t)(m_cap - pos0) : 0u;
             }
         }
         if (w == 0) w = 1;

@@ -113,12 +113,9 @@ def _texture(p):
     return np.clip(np.stack([r, g, b], 1) + stripes[:, None], 0.0, 1.0)
 
 
-def lidar_sweep(origin, lo, hi, n_beams=64, az_step_deg=0.2, elev=(-25.0, 15.0), rng_lim=(2.0, 60.0)):
-    """Ray-cast one 360-degree sweep against the ground plane z=0 and the boxes."""
-    el = np.deg2rad(np.linspace(elev[0], elev[1], n_beams))
-    az = np.deg2rad(np.arange(0.0, 360.0, az_step_deg))
-    E, A = np.meshgrid(el, az, indexing="ij")
-    d = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+def _ray_cast(origin, d, lo, hi):
+    """Distance along unit directions d from origin to the first hit of the
+    ground plane z=0 or a box (inf where a ray hits nothing)."""
     tbest = np.full(d.shape[0], np.inf)
     down = d[:, 2] < 0
     tbest[down] = origin[2] / (-d[down, 2])
@@ -131,8 +128,27 @@ def lidar_sweep(origin, lo, hi, n_beams=64, az_step_deg=0.2, elev=(-25.0, 15.0),
         tmax = np.maximum(t0, t1).min(2)
         tmin = np.where((tmax >= tmin) & (tmin > 0), tmin, np.inf).min(1)
         tbest[sl] = np.minimum(tbest[sl], tmin)
+    return tbest
+
+
+def lidar_sweep(origin, lo, hi, n_beams=64, az_step_deg=0.2, elev=(-25.0, 15.0), rng_lim=(2.0, 60.0)):
+    """Ray-cast one 360-degree sweep against the ground plane z=0 and the boxes."""
+    el = np.deg2rad(np.linspace(elev[0], elev[1], n_beams))
+    az = np.deg2rad(np.arange(0.0, 360.0, az_step_deg))
+    E, A = np.meshgrid(el, az, indexing="ij")
+    d = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    tbest = _ray_cast(origin, d, lo, hi)
     keep = (tbest >= rng_lim[0]) & (tbest <= rng_lim[1])
     return origin + d[keep] * tbest[keep, None]
+
+
+def world(seed=BASE_SEED + 2):
+    """The ground and box facades of the LiDAR scenes drawn with ``seed``
+    (the same draw as ``lidar_scene``), and its trajectory phase."""
+    rng = _rng(seed)
+    lo, hi = _boxes(rng)
+    phase = float(rng.uniform(0, 2 * math.pi))
+    return lo, hi, phase
 
 
 def trajectory_pose(s, seed_phase=0.0, length=50.0, height=1.8):
@@ -204,9 +220,7 @@ def fresh_scan(n, step, seed=BASE_SEED + 2):
     same ground and facades), taken at a seeded trajectory position for map
     expansion step ``step``: at most n points, in acquisition order, with their
     procedural colours in [0, 1].  Returns float32 (points [k,3], colours [k,3])."""
-    rng = _rng(seed)
-    lo, hi = _boxes(rng)
-    phase = float(rng.uniform(0, 2 * math.pi))
+    lo, hi, phase = world(seed)
     r2 = _rng(seed + 1000 + int(step))
     origin, _ = trajectory_pose(float(r2.uniform(0.05, 0.95)), phase)
     P = lidar_sweep(origin, lo, hi)
@@ -226,35 +240,90 @@ def trajectory_cameras(n_views, seed=BASE_SEED + 3, phase=0.0, W=1280, H=1024, f
     return cams
 
 
-def target_images(cam: CameraSpec, seed, lidar_frac=0.05, depth_range=(2.0, 60.0)):
-    """Level-0 targets for one keyframe: a structured colour image and sparse LiDAR depth.
+def camera_centre(cam: CameraSpec):
+    """World position of the camera: -R^T t."""
+    return -(np.asarray(cam.R, np.float64).T @ np.asarray(cam.t, np.float64))
 
-    The image is a smooth colour field with sharp bands and noise; the depth
-    target is nonzero on ``lidar_frac`` of the pixels, grouped in 64 scan
-    rows, with a smooth depth field in ``depth_range``.
-    """
-    rng = _rng(seed)
-    H, W = cam.H, cam.W
-    yy, xx = np.meshgrid(np.linspace(0, 1, H), np.linspace(0, 1, W), indexing="ij")
-    ph = rng.uniform(0, 2 * math.pi, 6)
-    img = np.stack([
-        0.5 + 0.3 * np.sin(7 * xx + ph[0]) * np.cos(5 * yy + ph[1]),
-        0.5 + 0.3 * np.sin(11 * xx * yy + ph[2]),
-        0.5 + 0.3 * np.cos(9 * yy + ph[3]) * np.sin(3 * xx + ph[4]),
-    ])
-    img += 0.15 * (np.sin(40 * xx + 13 * yy + ph[5]) > 0.6)
-    img += rng.normal(0, 0.03, img.shape)
-    img = np.clip(img, 0, 1).astype(np.float32)
-    depth = np.zeros((H, W), np.float32)
-    rows = np.linspace(H * 0.35, H - 1, 64).astype(int)
-    k = int(lidar_frac * H * W)
-    per_row = max(1, k // rows.shape[0])
-    field = depth_range[0] + (depth_range[1] - depth_range[0]) * (
-        0.5 + 0.5 * np.sin(3 * xx + ph[0]) * np.cos(2 * yy + ph[1]))
-    for r in rows:
-        cols = rng.choice(W, size=min(W, per_row), replace=False)
-        depth[r, cols] = field[r, cols]
-    return img, depth
+
+def camera_image(cam: CameraSpec, seed, world_seed=BASE_SEED + 2, noise=0.01):
+    """What the keyframe camera sees of the LiDAR scenes' world: each pixel's
+    ray (through the pixel's integer coordinate) is cast against the ground
+    and the facades and takes the procedural colour of the hit point, the
+    colour the map's LiDAR points carry; rays that hit nothing within 200 m
+    see a sky gradient.  Seeded sensor noise N(0, noise), clipped to [0, 1]."""
+    lo, hi, _ = world(world_seed)
+    R = np.asarray(cam.R, np.float64)
+    C = camera_centre(cam)
+    ys, xs = np.mgrid[0:cam.H, 0:cam.W]
+    dc = np.stack([(xs - cam.cx) / cam.fx, (ys - cam.cy) / cam.fy, np.ones_like(xs, np.float64)], -1)
+    d = dc @ R  # R^T d_cam, per pixel
+    d /= np.linalg.norm(d, axis=2, keepdims=True)
+    t = np.full((cam.H, cam.W), np.inf)
+    down = d[..., 2] < 0
+    t[down] = C[2] / (-d[..., 2][down])
+    # each facade only where its projected bounding rectangle lies
+    for b in range(lo.shape[0]):
+        corners = np.array([[x, y, z] for x in (lo[b, 0], hi[b, 0]) for y in (lo[b, 1], hi[b, 1])
+                            for z in (lo[b, 2], hi[b, 2])])
+        pc = corners @ R.T + np.asarray(cam.t, np.float64)
+        if (pc[:, 2] <= 0).all():
+            continue
+        if (pc[:, 2] <= 1e-3).any():
+            x0, x1, y0, y1 = 0, cam.W, 0, cam.H
+        else:
+            u = cam.fx * pc[:, 0] / pc[:, 2] + cam.cx
+            v = cam.fy * pc[:, 1] / pc[:, 2] + cam.cy
+            x0, x1 = max(0, int(np.floor(u.min()))), min(cam.W, int(np.ceil(u.max())) + 1)
+            y0, y1 = max(0, int(np.floor(v.min()))), min(cam.H, int(np.ceil(v.max())) + 1)
+            if x0 >= x1 or y0 >= y1:
+                continue
+        db = d[y0:y1, x0:x1]
+        inv = 1.0 / np.where(np.abs(db) < 1e-12, 1e-12, db)
+        t0 = (lo[b] - C) * inv
+        t1 = (hi[b] - C) * inv
+        tmin = np.minimum(t0, t1).max(-1)
+        tmax = np.maximum(t0, t1).min(-1)
+        tb = np.where((tmax >= tmin) & (tmin > 0), tmin, np.inf)
+        t[y0:y1, x0:x1] = np.minimum(t[y0:y1, x0:x1], tb)
+    d = d.reshape(-1, 3)
+    t = t.reshape(-1)
+    hit = np.isfinite(t) & (t < 200.0)
+    img = np.empty((d.shape[0], 3))
+    img[hit] = _texture(C + d[hit] * t[hit, None])
+    up = np.clip(d[~hit, 2], 0.0, 1.0)[:, None]
+    img[~hit] = np.array([0.62, 0.74, 0.90]) * (1 - up) + np.array([0.30, 0.45, 0.80]) * up
+    img = img.reshape(cam.H, cam.W, 3).transpose(2, 0, 1)
+    img = img + _rng(seed).normal(0.0, noise, img.shape)
+    return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def lidar_depth_image(cam: CameraSpec, world_seed=BASE_SEED + 2, z_near=0.2):
+    """Sparse LiDAR depth target of a keyframe: one sweep of the world taken
+    from the camera's position, projected into the camera (pinhole, nearest
+    pixel), keeping the nearest return per pixel (a z-buffer).  Values are
+    view-space depths; pixels without a return hold 0."""
+    lo, hi, _ = world(world_seed)
+    C = camera_centre(cam)
+    P = lidar_sweep(C, lo, hi)
+    R = np.asarray(cam.R, np.float64)
+    pc = P @ R.T + np.asarray(cam.t, np.float64)
+    z = pc[:, 2]
+    front = z > z_near
+    u = np.rint(cam.fx * pc[front, 0] / z[front] + cam.cx).astype(np.int64)
+    v = np.rint(cam.fy * pc[front, 1] / z[front] + cam.cy).astype(np.int64)
+    zf = z[front]
+    inb = (u >= 0) & (u < cam.W) & (v >= 0) & (v < cam.H)
+    depth = np.full(cam.H * cam.W, np.inf)
+    np.minimum.at(depth, v[inb] * cam.W + u[inb], zf[inb])
+    depth[~np.isfinite(depth)] = 0.0
+    return depth.reshape(cam.H, cam.W).astype(np.float32)
+
+
+def target_images(cam: CameraSpec, seed, world_seed=BASE_SEED + 2):
+    """Level-0 targets of one keyframe of the LiDAR scenes: the camera's image
+    of the world (``camera_image``, noise seeded by ``seed``) and the sparse
+    LiDAR depth of a sweep from the keyframe's position (``lidar_depth_image``)."""
+    return camera_image(cam, seed, world_seed), lidar_depth_image(cam, world_seed)
 
 
 def mixed_level_views(n_views, seed=BASE_SEED + 4, levels=(0, 1, 2)):
