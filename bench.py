@@ -291,33 +291,40 @@ def run_ours(args):
     stats = lv.step_stats()
     _, kernels_per_step = lv.profile_read()
 
-    # plain path: 8 sequential single-view calls (render, loss, backward) per step
-    ms_plain = None
+    # plain path: 8 sequential single-view calls (render, loss, backward) per step,
+    # with renders that do not wait on the stream (lists sized from the earlier
+    # renders of the context), and with renders that wait once each to size them
+    ms_plain = ms_plain_sync = None
     if not args.skip_plain:
         pgrads = {k: torch.zeros_like(dev[k]) for k in P.PARAM_NAMES}
 
-        def plain_step():
+        def plain_step(wait):
             for i, (c, l) in enumerate(zip(cams, levels)):
                 g_l, d_l = gts[i], lis[i]
                 for _ in range(l):
                     g_l, d_l = lv.pyramid_down(g_l, d_l)
-                rgb, depth, alpha, slot = lv.render(dev, c, l)
+                rgb, depth, alpha, slot = lv.render(dev, c, l, wait=wait)
                 _, d_rgb, d_dep = lv.loss(rgb, depth, g_l, d_l, lam, lamd)
                 lv.backward(slot, dev, d_rgb, d_dep, grads=pgrads, accumulate=i > 0)
                 lv.release(slot)
 
-        for _ in range(2):
-            plain_step()
-        torch.cuda.synchronize()
-        kp = max(3, args.steps // 4)
-        barrier()
-        e0.record(stream)
-        for _ in range(kp):
-            plain_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms_plain = max_over_ranks(e0.elapsed_time(e1) / kp)
+        def time_plain(wait):
+            for _ in range(2):
+                plain_step(True)
+            torch.cuda.synchronize()
+            kp = max(3, args.steps // 4)
+            barrier()
+            e0.record(stream)
+            for _ in range(kp):
+                plain_step(wait)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            lv.sync_status()
+            return max_over_ranks(e0.elapsed_time(e1) / kp)
+
+        ms_plain = time_plain(False)
+        ms_plain_sync = time_plain(True)
 
     # per-phase device time of the same step enqueued eagerly (events per phase)
     lv.profile(True)
@@ -431,6 +438,8 @@ def run_ours(args):
         "mpix_per_s": round(world * pix * steps_per_s / 1e6, 3),
         "plain_ms_per_step": None if ms_plain is None else round(ms_plain, 4),
         "batched_vs_plain": None if ms_plain is None else round(ms_plain / ms_batched, 3),
+        "plain_sync_ms_per_step": None if ms_plain_sync is None else round(ms_plain_sync, 4),
+        "batched_vs_plain_sync": None if ms_plain_sync is None else round(ms_plain_sync / ms_batched, 3),
         "e2e": {"value": round(world / t_e2e["pipelined"], 4), "unit": "train steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "copies": "each step's targets copied from pinned host memory on a second stream while the "
