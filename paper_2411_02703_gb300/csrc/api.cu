@@ -84,7 +84,7 @@ struct lvigs_ctx {
 
     // shared temporaries (one stream at a time per context)
     DevBuf pos, ck, cv, ck2, cv2, scan_tmp, radix_tmp, status, g2d, loss_tmp, stats;
-    uint32_t *host_counters = nullptr; // pinned [4]
+    uint32_t *host_counters = nullptr; // pinned [8]
     uint32_t *host_status = nullptr;   // pinned [1]
 
     std::vector<RenderState *> slots;
@@ -124,7 +124,7 @@ struct lvigs_ctx {
     // map maintenance (append / prune) scratch, kept apart from the step's
     // buffers so that growing it does not invalidate the step's graph
     DevBuf mp_pts, mp_col, mp_keep, mp_offs, mp_keys, mp_vals, mp_keys2, mp_vals2, mp_scan, mp_radix, mp_cells,
-        mp_logs, mp_small, mp_tmp;
+        mp_logs, mp_small, mp_tmp, mp_spts;
 
     // opt-in per-phase device timing of eagerly enqueued work
     bool prof = false;
@@ -505,7 +505,7 @@ lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
     ctx->cfg = c;
     ctx->bm = bm;
     cudaError_t e = cudaGetDevice(&ctx->device);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_counters, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_counters, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_status, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_losses, kMaxViews * 4 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->host_batch_counters, 4 * sizeof(uint32_t));
@@ -545,7 +545,7 @@ void lvigs_destroy(lvigs_ctx *ctx) {
                         &ctx->img_alpha, &ctx->d_rgb, &ctx->d_depth, &ctx->mp_pts,
                         &ctx->mp_col, &ctx->mp_keep, &ctx->mp_offs, &ctx->mp_keys, &ctx->mp_vals, &ctx->mp_keys2,
                         &ctx->mp_vals2, &ctx->mp_scan, &ctx->mp_radix, &ctx->mp_cells, &ctx->mp_logs,
-                        &ctx->mp_small, &ctx->mp_tmp};
+                        &ctx->mp_small, &ctx->mp_tmp, &ctx->mp_spts};
     for (DevBuf *b : shared) release(ctx, *b);
     for (int v = 0; v < kMaxViews; ++v) {
         release(ctx, ctx->gt_stage[v]);
@@ -1438,9 +1438,10 @@ lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const f
     if (k == 0) return LVIGS_OK;
 
     const float *src_pts = points, *src_col = colours;
-    int64_t kk = k;
     LV_TRY(ensure(ctx, ctx->mp_small, 64));
     uint32_t *small = (uint32_t *)ctx->mp_small.p; // [0] count, [2..8) box
+    int *box = (int *)(small + 2);
+    const uint32_t *dev_count = nullptr;
     if (alpha) {
         const ViewDesc v = make_view(*cam, level, 16, 16);
         PointCamera C{};
@@ -1462,24 +1463,20 @@ lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const f
         launch_point_filter(points, k, C, alpha, cfg.tau_alpha, cfg.filter_literal, keep, s);
         launch_scan(keep, nullptr, 1, offs, offs + k, nullptr, k, (uint32_t *)ctx->mp_scan.p, s);
         launch_gather_points(points, colours, k, keep, offs, (float *)ctx->mp_pts.p, (float *)ctx->mp_col.p, s);
-        LV_CUDA(cudaMemcpyAsync(ctx->host_counters, offs + k, 4, cudaMemcpyDeviceToHost, s));
-        LV_CUDA(cudaStreamSynchronize(s));
-        kk = ctx->host_counters[0];
         src_pts = (const float *)ctx->mp_pts.p;
         src_col = (const float *)ctx->mp_col.p;
-        if (kk == 0) return LVIGS_OK;
+        dev_count = offs + k;
     }
 
-    // bounding box -> grid
-    int *box = (int *)(small + 2);
-    launch_bbox(src_pts, kk, box, s);
+    // bounding box of the kept points -> grid; one wait reads the count and the box
+    launch_bbox(src_pts, k, dev_count, box, s);
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, box, 24, cudaMemcpyDeviceToHost, s));
+    if (dev_count) LV_CUDA(cudaMemcpyAsync(ctx->host_counters + 6, dev_count, 4, cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const int64_t kk = dev_count ? (int64_t)ctx->host_counters[6] : k;
+    if (kk == 0) return LVIGS_OK;
     int hbox[6];
-    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, box, 16, cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(hbox, ctx->host_counters, 16);
-    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, box + 4, 8, cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(hbox + 4, ctx->host_counters, 8);
+    std::memcpy(hbox, ctx->host_counters, 24);
     float lo[3], hi[3];
     for (int a = 0; a < 3; ++a) {
         lo[a] = ord_to_float(hbox[a]);
@@ -1499,6 +1496,7 @@ lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const f
     LV_TRY(ensure(ctx, ctx->mp_radix, radix_tmp_words(kk) * 4));
     LV_TRY(ensure(ctx, ctx->mp_cells, (size_t)n_cells * sizeof(uint2)));
     LV_TRY(ensure(ctx, ctx->mp_logs, (size_t)kk * 4));
+    LV_TRY(ensure(ctx, ctx->mp_spts, (size_t)kk * sizeof(float4)));
     uint32_t *keys = (uint32_t *)ctx->mp_keys.p, *vals = (uint32_t *)ctx->mp_vals.p;
     uint32_t *keys2 = (uint32_t *)ctx->mp_keys2.p, *vals2 = (uint32_t *)ctx->mp_vals2.p;
     launch_cell_keys(src_pts, kk, G, keys, vals, s);
@@ -1506,7 +1504,8 @@ lvigs_status lvigs_append_gaussians(lvigs_ctx *ctx, const float *points, const f
     const uint32_t *skeys = alt ? keys2 : keys, *svals = alt ? vals2 : vals;
     launch_set_u32(small, (uint32_t)kk, s);
     launch_ranges(skeys, small, kk, (uint2 *)ctx->mp_cells.p, n_cells, s);
-    launch_knn(src_pts, kk, G, (const uint2 *)ctx->mp_cells.p, svals, cfg.min_dist2, (float *)ctx->mp_logs.p, s);
+    launch_knn(src_pts, kk, G, (const uint2 *)ctx->mp_cells.p, svals, (float4 *)ctx->mp_spts.p, cfg.min_dist2,
+               (float *)ctx->mp_logs.p, s);
 
     const ParamBufs P{params->means, params->log_scales, params->quats, params->opacity_logits, params->sh};
     ParamBufs Mb{}, Vb{};
@@ -1543,23 +1542,33 @@ lvigs_status lvigs_prune_gaussians(lvigs_ctx *ctx, float min_opacity, const lvig
     uint32_t *keep = (uint32_t *)ctx->mp_keep.p, *offs = (uint32_t *)ctx->mp_offs.p;
     launch_prune_flags(params->opacity_logits, n, thr, keep, s);
     launch_scan(keep, nullptr, 1, offs, offs + n, nullptr, n, (uint32_t *)ctx->mp_scan.p, s);
-    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, offs + n, 4, cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
-    const int64_t kept = ctx->host_counters[0];
-    if (kept == n) return LVIGS_OK;
+    // every buffer compacted through its own scratch segment; the kernels read
+    // the kept count on the device, so the only wait is for the count returned
     const int widths[5] = {3, 3, 4, 1, 3 * sh_stride_k};
-    LV_TRY(ensure(ctx, ctx->mp_tmp, (size_t)n * widths[4] * 4));
-    float *tmp = (float *)ctx->mp_tmp.p;
+    PruneArgs A{};
+    A.n = n;
+    A.keep = keep;
+    A.offs = offs;
+    size_t words = 0, seg_off[kPruneSegs];
     const lvigs_param_buffers *sets[3] = {params, exp_avg, exp_avg_sq};
     for (const lvigs_param_buffers *b : sets) {
         if (!b) continue;
         float *bufs[5] = {b->means, b->log_scales, b->quats, b->opacity_logits, b->sh};
         for (int f = 0; f < 5; ++f) {
-            launch_compact_rows(bufs[f], tmp, n, widths[f], keep, offs, s);
-            if (kept > 0)
-                LV_CUDA(cudaMemcpyAsync(bufs[f], tmp, (size_t)kept * widths[f] * 4, cudaMemcpyDeviceToDevice, s));
+            seg_off[A.nseg] = words;
+            PruneSeg &S = A.seg[A.nseg++];
+            S.buf = bufs[f];
+            S.w = widths[f];
+            S.vec = ((uintptr_t)bufs[f] & 15) == 0;
+            words += ((size_t)n * widths[f] + 3) & ~(size_t)3; // segments start 16-byte aligned
         }
     }
+    LV_TRY(ensure(ctx, ctx->mp_tmp, words * 4));
+    for (int i = 0; i < A.nseg; ++i) A.seg[i].tmp = (float *)ctx->mp_tmp.p + seg_off[i];
+    launch_prune_compact(A, s);
+    LV_CUDA(cudaMemcpyAsync(ctx->host_counters, offs + n, 4, cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const int64_t kept = ctx->host_counters[0];
     LV_CUDA(cudaGetLastError());
     *n_out = kept;
     return LVIGS_OK;

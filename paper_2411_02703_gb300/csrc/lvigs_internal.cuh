@@ -311,7 +311,8 @@ void launch_point_filter(const float *pts, int64_t k, const PointCamera &C, cons
 void launch_gather_points(const float *pts, const float *col, int64_t k, const uint32_t *keep, const uint32_t *offs,
                           float *pts_out, float *col_out, cudaStream_t s);
 // box: 6 ints, ordered-integer images of (min xyz, max xyz); ord_to_float decodes them.
-void launch_bbox(const float *pts, int64_t k, int *box, cudaStream_t s);
+// With count (device, may be null) only the first *count of the k points are taken.
+void launch_bbox(const float *pts, int64_t k, const uint32_t *count, int *box, cudaStream_t s);
 float ord_to_float(int o);
 
 // Uniform grid of the neighbour search: origin o, cell size h, D cells per axis.
@@ -321,14 +322,29 @@ struct KnnGrid {
     int D[3];
 };
 void launch_cell_keys(const float *pts, int64_t k, const KnnGrid &G, uint32_t *keys, uint32_t *vals, cudaStream_t s);
+// spts: k float4 of scratch (the points in cell order).
 void launch_knn(const float *pts, int64_t k, const KnnGrid &G, const uint2 *cells, const uint32_t *order,
-                float min_dist2, float *log_scales_out, cudaStream_t s);
+                float4 *spts, float min_dist2, float *log_scales_out, cudaStream_t s);
 void launch_init_rows(const float *pts, const float *col, const float *log_s, int64_t k, int64_t n0,
                       const ParamBufs &P, const ParamBufs &M, const ParamBufs &V, int K, float opacity_logit,
                       float inv_c0, cudaStream_t s);
 void launch_set_u32(uint32_t *p, uint32_t v, cudaStream_t s);
 void launch_prune_flags(const float *logits, int64_t n, float thr, uint32_t *keep, cudaStream_t s);
-void launch_compact_rows(const float *src, float *dst, int64_t n, int w, const uint32_t *keep, const uint32_t *offs,
-                         cudaStream_t s);
+// Pruning of up to three sets of the five parameter buffers at once: kept
+// rows (keep[r] = 1) move to row offs[r]; the kept count offs[n] is read on
+// the device.  tmp: a scratch segment per buffer (n * w floats, 16-byte aligned).
+constexpr int kPruneSegs = 15;
+struct PruneSeg {
+    float *buf, *tmp;
+    int w;   // floats per row
+    int vec; // buf 16-byte aligned
+};
+struct PruneArgs {
+    PruneSeg seg[kPruneSegs];
+    int nseg;
+    int64_t n;
+    const uint32_t *keep, *offs;
+};
+void launch_prune_compact(const PruneArgs &A, cudaStream_t s);
 
 } // namespace lvigs

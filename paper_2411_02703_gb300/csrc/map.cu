@@ -12,6 +12,7 @@
 // search is exact: points are bucketed in a uniform grid (radix sort by cell)
 // and every query scans cubic shells of cells around its own until its third
 // distance is inside the scanned radius.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -120,7 +121,10 @@ __global__ void bbox_init_kernel(int *box) {
     if (threadIdx.x < 6) box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
 }
 
-__global__ void bbox_kernel(const float *__restrict__ pts, int64_t k, int *__restrict__ box) {
+// k bounds the points; when count is given, only the first *count are taken.
+__global__ void bbox_kernel(const float *__restrict__ pts, int64_t k, const uint32_t *__restrict__ count,
+                            int *__restrict__ box) {
+    if (count) k = min(k, (int64_t)*count);
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
@@ -177,77 +181,124 @@ __device__ __forceinline__ void push3(float d, float best[3], int &cnt) {
     }
 }
 
-// Scan the points of the cells in x-row [x0, x1] of (cy, cz).
-__device__ __forceinline__ void scan_row(const float *__restrict__ pts, const uint2 *__restrict__ cells,
-                                         const uint32_t *__restrict__ order, const KnnGrid &G, int cy, int cz, int x0,
-                                         int x1, uint32_t self, float qx, float qy, float qz, float best[3],
-                                         int &cnt) {
+// Points in cell order, with the position of each in the input as .w bits.
+__global__ void gather_sorted_kernel(const float *__restrict__ pts, int64_t k, const uint32_t *__restrict__ order,
+                                     float4 *__restrict__ spts) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = order[j];
+        spts[j] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __uint_as_float(i));
+    }
+}
+
+// Lane-parallel scan of the points of the cells in x-row [x0, x1] of (cy, cz):
+// the lanes read the row's cell ranges together (the cells of a row are
+// consecutive ids, so their points are one run of the sorted order), then
+// split the run; each lane keeps its own three smallest squared distances.
+__device__ __forceinline__ void scan_row_warp(const float4 *__restrict__ spts, const uint2 *__restrict__ cells,
+                                              const KnnGrid &G, int cy, int cz, int x0, int x1, uint32_t self,
+                                              float qx, float qy, float qz, float best[3], int &cnt, int lane) {
     x0 = max(x0, 0);
     x1 = min(x1, G.D[0] - 1);
     if (cy < 0 || cy >= G.D[1] || cz < 0 || cz >= G.D[2] || x0 > x1) return;
     const uint32_t row = ((uint32_t)cz * (uint32_t)G.D[1] + (uint32_t)cy) * (uint32_t)G.D[0];
-    // the cells of a row are consecutive ids, so their points are one run of the sorted order
     uint32_t start = 0xffffffffu, end = 0;
-    for (int x = x0; x <= x1; ++x) {
-        const uint2 r = cells[row + x];
-        if (r.y > r.x) {
-            if (start == 0xffffffffu) start = r.x;
-            end = r.y;
+    for (int xb = x0; xb <= x1; xb += 32) {
+        const int x = xb + lane;
+        uint2 r = make_uint2(0, 0);
+        if (x <= x1) r = cells[row + x];
+        const unsigned nz = __ballot_sync(0xffffffffu, r.y > r.x);
+        if (nz) {
+            const uint32_t first = __shfl_sync(0xffffffffu, r.x, __ffs(nz) - 1);
+            const uint32_t last = __shfl_sync(0xffffffffu, r.y, 31 - __clz(nz));
+            if (start == 0xffffffffu) start = first;
+            end = last;
         }
     }
     if (start == 0xffffffffu) return;
-    for (uint32_t j = start; j < end; ++j) {
-        const uint32_t idx = order[j];
-        if (idx == self) continue;
-        const float dx = pts[3 * idx] - qx, dy = pts[3 * idx + 1] - qy, dz = pts[3 * idx + 2] - qz;
+    for (uint32_t j = start + lane; j < end; j += 32) {
+        if (j == self) continue;
+        const float4 p = spts[j];
+        const float dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
         push3(dx * dx + dy * dy + dz * dz, best, cnt);
     }
 }
 
-// One thread per point, in cell order (neighbouring threads scan the same
-// cells).  After the shells up to r are scanned, every point within r*h of
-// the query has been seen (same cell arithmetic for all points; 0.99 absorbs
-// the binary32 rounding of the cell coordinates), so the search stops once the
+// The warp's three smallest of the lanes' lists (as a multiset, ascending)
+// and how many candidates the warp has seen, capped at 3.
+__device__ __forceinline__ void warp_top3(const float best[3], int cnt, int lane, float top[3], int &tot) {
+    int head = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float mine = head == 0 ? best[0] : (head == 1 ? best[1] : (head == 2 ? best[2] : INFINITY));
+        float m = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        top[q] = m;
+        const unsigned own = __ballot_sync(0xffffffffu, mine == m && head < 3);
+        if (own && lane == __ffs(own) - 1) ++head;
+    }
+    int c = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    tot = min(c, 3);
+}
+
+// One warp per point, in cell order (neighbouring warps scan the same cells).
+// After the shells up to r are scanned, every point within r*h of the query
+// has been seen (same cell arithmetic for all points; 0.99 absorbs the
+// binary32 rounding of the cell coordinates), so the search stops once the
 // wanted neighbours are all within that radius.
-__global__ void __launch_bounds__(128) knn_kernel(const float *__restrict__ pts, int64_t k, KnnGrid G,
-                                                  const uint2 *__restrict__ cells, const uint32_t *__restrict__ order,
-                                                  float min_dist2, float *__restrict__ log_scales_out) {
+__global__ void __launch_bounds__(256, 4) knn_kernel(const float4 *__restrict__ spts, int64_t k, KnnGrid G,
+                                                  const uint2 *__restrict__ cells, float min_dist2,
+                                                  float *__restrict__ log_scales_out) {
+    const int lane = threadIdx.x & 31;
     const int want = (int)(k - 1 < 3 ? k - 1 : 3);
     const int rmax = max(G.D[0], max(G.D[1], G.D[2]));
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t i = order[j];
-        const float qx = pts[3 * i], qy = pts[3 * i + 1], qz = pts[3 * i + 2];
-        const int cx = cell_coord(qx, G.o[0], G.inv_h, G.D[0]);
-        const int cy = cell_coord(qy, G.o[1], G.inv_h, G.D[1]);
-        const int cz = cell_coord(qz, G.o[2], G.inv_h, G.D[2]);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); j < k; j += warps) {
+        const float4 q = spts[j];
+        const int cx = cell_coord(q.x, G.o[0], G.inv_h, G.D[0]);
+        const int cy = cell_coord(q.y, G.o[1], G.inv_h, G.D[1]);
+        const int cz = cell_coord(q.z, G.o[2], G.inv_h, G.D[2]);
         float best[3] = {INFINITY, INFINITY, INFINITY};
+        float top[3] = {INFINITY, INFINITY, INFINITY};
         int cnt = 0;
+        const uint32_t self = (uint32_t)j;
         if (want > 0) {
             for (int r = 0; r <= rmax; ++r) {
                 for (int dz = -r; dz <= r; ++dz) {
                     const bool zface = (dz == -r || dz == r);
                     for (int dy = -r; dy <= r; ++dy) {
                         if (zface || dy == -r || dy == r) {
-                            scan_row(pts, cells, order, G, cy + dy, cz + dz, cx - r, cx + r, i, qx, qy, qz, best, cnt);
+                            scan_row_warp(spts, cells, G, cy + dy, cz + dz, cx - r, cx + r, self, q.x, q.y, q.z,
+                                          best, cnt, lane);
                         } else {
-                            scan_row(pts, cells, order, G, cy + dy, cz + dz, cx - r, cx - r, i, qx, qy, qz, best, cnt);
+                            scan_row_warp(spts, cells, G, cy + dy, cz + dz, cx - r, cx - r, self, q.x, q.y, q.z,
+                                          best, cnt, lane);
                             if (r > 0)
-                                scan_row(pts, cells, order, G, cy + dy, cz + dz, cx + r, cx + r, i, qx, qy, qz, best,
-                                         cnt);
+                                scan_row_warp(spts, cells, G, cy + dy, cz + dz, cx + r, cx + r, self, q.x, q.y, q.z,
+                                              best, cnt, lane);
                         }
                     }
                 }
+                int tot;
+                warp_top3(best, cnt, lane, top, tot);
                 const float rad = 0.99f * (float)r * G.h;
-                if (cnt >= want && best[want - 1] <= rad * rad) break;
+                const float worst = want == 1 ? top[0] : (want == 2 ? top[1] : top[2]);
+                if (tot >= want && worst <= rad * rad) break;
             }
         }
-        float mean = 0.f;
-        if (want > 0) {
-            float s = 0.f;
-            for (int q = 0; q < want; ++q) s += best[q];
-            mean = s / (float)want;
+        if (lane == 0) {
+            float mean = 0.f;
+            if (want > 0) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+                    if (t < want) acc += top[t];
+                mean = acc / (float)want;
+            }
+            log_scales_out[__float_as_uint(q.w)] = 0.5f * logf(fmaxf(mean, min_dist2));
         }
-        log_scales_out[i] = 0.5f * logf(fmaxf(mean, min_dist2));
     }
 }
 
@@ -293,13 +344,43 @@ __global__ void prune_flags_kernel(const float *__restrict__ logits, int64_t n, 
         keep[i] = logits[i] >= thr ? 1u : 0u;
 }
 
-// dst row offs[r] <- src row r for kept rows (row = `w` floats).
-__global__ void compact_rows_kernel(const float *__restrict__ src, float *__restrict__ dst, int64_t n, int w,
-                                    const uint32_t *__restrict__ keep, const uint32_t *__restrict__ offs) {
-    const int64_t total = n * w;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / w;
-        if (keep[r]) dst[(int64_t)offs[r] * w + (e - r * w)] = src[e];
+// Pruning, first pass: the kept rows of every buffer (blockIdx.y picks the
+// buffer) to consecutive rows of its scratch segment.  Rows are taken in
+// chunks of kPruneRows so the row of an element comes from a 32-bit divide.
+// Nothing is done when every row is kept (offs[n] == n).
+constexpr int kPruneRows = 256;
+__global__ void __launch_bounds__(256) prune_compact_kernel(PruneArgs A) {
+    const int64_t n = A.n;
+    if ((int64_t)A.offs[n] == n) return;
+    const PruneSeg S = A.seg[blockIdx.y];
+    const uint32_t w = (uint32_t)S.w;
+    for (int64_t r0 = (int64_t)blockIdx.x * kPruneRows; r0 < n; r0 += (int64_t)gridDim.x * kPruneRows) {
+        const uint32_t rows = (uint32_t)min((int64_t)kPruneRows, n - r0);
+        const float *src = S.buf + r0 * w;
+        for (uint32_t e = threadIdx.x; e < rows * w; e += blockDim.x) {
+            const uint32_t r = e / w;
+            if (A.keep[r0 + r]) S.tmp[(int64_t)A.offs[r0 + r] * w + (e - r * w)] = src[e];
+        }
+    }
+}
+
+// Second pass: the first offs[n] rows of each scratch segment back over the
+// buffer (float4 where the buffer allows it; the segments are 16-byte aligned).
+__global__ void __launch_bounds__(256) prune_copy_back_kernel(PruneArgs A) {
+    const int64_t n = A.n;
+    const int64_t kept = A.offs[n];
+    if (kept == n) return;
+    const PruneSeg S = A.seg[blockIdx.y];
+    const int64_t len = kept * S.w;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (S.vec) {
+        const int64_t units = len >> 2;
+        for (int64_t u = t0; u < units; u += stride)
+            ((float4 *)S.buf)[u] = ((const float4 *)S.tmp)[u];
+        for (int64_t e = (units << 2) + t0; e < len; e += stride) S.buf[e] = S.tmp[e];
+    } else {
+        for (int64_t e = t0; e < len; e += stride) S.buf[e] = S.tmp[e];
     }
 }
 
@@ -330,10 +411,10 @@ void launch_gather_points(const float *pts, const float *col, int64_t k, const u
     gather_points_kernel<<<blocks_for(k, 256), 256, 0, s>>>(pts, col, k, keep, offs, pts_out, col_out);
 }
 
-void launch_bbox(const float *pts, int64_t k, int *box, cudaStream_t s) {
+void launch_bbox(const float *pts, int64_t k, const uint32_t *count, int *box, cudaStream_t s) {
     bbox_init_kernel<<<1, 32, 0, s>>>(box);
     if (k <= 0) return;
-    bbox_kernel<<<blocks_for(k, 256), 256, 0, s>>>(pts, k, box);
+    bbox_kernel<<<blocks_for(k, 256), 256, 0, s>>>(pts, k, count, box);
 }
 
 float ord_to_float(int o) {
@@ -349,9 +430,10 @@ void launch_cell_keys(const float *pts, int64_t k, const KnnGrid &G, uint32_t *k
 }
 
 void launch_knn(const float *pts, int64_t k, const KnnGrid &G, const uint2 *cells, const uint32_t *order,
-                float min_dist2, float *log_scales_out, cudaStream_t s) {
+                float4 *spts, float min_dist2, float *log_scales_out, cudaStream_t s) {
     if (k <= 0) return;
-    knn_kernel<<<blocks_for(k, 128, 16), 128, 0, s>>>(pts, k, G, cells, order, min_dist2, log_scales_out);
+    gather_sorted_kernel<<<blocks_for(k, 256), 256, 0, s>>>(pts, k, order, spts);
+    knn_kernel<<<blocks_for(k * 32, 256), 256, 0, s>>>(spts, k, G, cells, min_dist2, log_scales_out);
 }
 
 void launch_init_rows(const float *pts, const float *col, const float *log_s, int64_t k, int64_t n0,
@@ -368,10 +450,14 @@ void launch_prune_flags(const float *logits, int64_t n, float thr, uint32_t *kee
     prune_flags_kernel<<<blocks_for(n, 256), 256, 0, s>>>(logits, n, thr, keep);
 }
 
-void launch_compact_rows(const float *src, float *dst, int64_t n, int w, const uint32_t *keep, const uint32_t *offs,
-                         cudaStream_t s) {
-    if (n <= 0) return;
-    compact_rows_kernel<<<blocks_for(n * w, 256, 16), 256, 0, s>>>(src, dst, n, w, keep, offs);
+void launch_prune_compact(const PruneArgs &A, cudaStream_t s) {
+    if (A.n <= 0 || A.nseg <= 0) return;
+    const int sms = device_sm_count();
+    const int64_t chunks = (A.n + kPruneRows - 1) / kPruneRows;
+    const int gx1 = (int)std::min<int64_t>(chunks, std::max<int64_t>(1, (int64_t)sms * 8 / A.nseg));
+    prune_compact_kernel<<<dim3(gx1, A.nseg), 256, 0, s>>>(A);
+    const int gx2 = std::max(1, sms * 8 / A.nseg);
+    prune_copy_back_kernel<<<dim3(gx2, A.nseg), 256, 0, s>>>(A);
 }
 
 } // namespace lvigs

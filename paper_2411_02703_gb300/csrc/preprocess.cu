@@ -11,8 +11,9 @@
 // contracted), so the keys are reproducible bit for bit on any IEEE machine.
 //
 // Backward, one warp per 32 Gaussians: the visible (view, Gaussian) pairs are
-// dealt out over the lanes and summed per Gaussian in shared memory, so the
-// parameter gradients need no global atomics.
+// dealt out over the lanes and summed per Gaussian in shared memory (plain
+// adds, the lanes of one owner taking turns), so the parameter gradients need
+// no atomics.
 #include <cmath>
 
 #include "lvigs_internal.cuh"
@@ -493,7 +494,10 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
 // lane per Gaussian idling through the views it does not see.  The worker lane
 // takes the owner's mean and Sigma by shuffle and its SH row from shared
 // memory (staged with coalesced loads), and adds its terms to the owner's
-// accumulators in shared memory.  The owner then finishes the per-Gaussian
+// accumulators in shared memory.  A round of 32 pairs spans a few views, so
+// an owner can appear in several lanes of it: those lanes add in lane order,
+// one turn each (match_any ranks them), which keeps the adds plain (a
+// shared-memory float atomic costs far more) and the sums deterministic.  The owner then finishes the per-Gaussian
 // part (Sigma -> scale, rotation; opacity) and the warp writes the SH
 // gradient rows back coalesced.
 // ---------------------------------------------------------------------------
@@ -608,142 +612,165 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
         float S6[6];
 #pragma unroll
         for (int t = 0; t < 6; ++t) S6[t] = __shfl_sync(0xffffffffu, Sg6[t], src);
-        if (!has) continue;
-        const size_t o = (size_t)vi * N + (size_t)(g0 + src);
-        const GGrad gg = g2d[o];
-        const float mx_ = gg.g0.x, my_ = gg.g0.y, mxx = gg.g0.z, mxy = gg.g0.w;
-        const float myy = gg.g1.x, dop = gg.g1.y, ddepth = gg.g1.z;
-        const float drgb[3] = {gg.g2.x, gg.g2.y, gg.g2.z};
-        if (mx_ == 0.f && my_ == 0.f && mxx == 0.f && mxy == 0.f && myy == 0.f && dop == 0.f &&
-            ddepth == 0.f && drgb[0] == 0.f && drgb[1] == 0.f && drgb[2] == 0.f)
-            continue;
-        const float Sg[3][3] = {{S6[0], S6[1], S6[2]}, {S6[1], S6[3], S6[4]}, {S6[2], S6[4], S6[5]}};
-        const ViewDesc &V = vsp->v[vi];
-        const float px = V.R[0] * gx + V.R[1] * gy + V.R[2] * gz + V.t[0];
-        const float py = V.R[3] * gx + V.R[4] * gy + V.R[5] * gz + V.t[1];
-        const float pz = V.R[6] * gx + V.R[7] * gy + V.R[8] * gz + V.t[2];
-        const float iz = 1.f / pz;
-        const float xz = px * iz, yz = py * iz;
-        const bool clx = xz < -V.limx || xz > V.limx;
-        const bool cly = yz < -V.limy || yz > V.limy;
-        const float txc = fminf(V.limx, fmaxf(-V.limx, xz));
-        const float tyc = fminf(V.limy, fmaxf(-V.limy, yz));
-        const float J00 = V.fx * iz, J02 = -V.fx * txc * iz;
-        const float J11 = V.fy * iz, J12 = -V.fy * tyc * iz;
-        float T[2][3];
+        // this pair's terms for its owner's accumulators
+        float t_sig[6], dm[3] = {0.f, 0.f, 0.f}, dop = 0.f, Y[16], m3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            T[0][j] = J00 * V.R[j] + J02 * V.R[6 + j];
-            T[1][j] = J11 * V.R[3 + j] + J12 * V.R[6 + j];
+        for (int t = 0; t < 6; ++t) t_sig[t] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) Y[k] = 0.f;
+        bool active = false;
+        GGrad gg;
+        if (has) {
+            gg = g2d[(size_t)vi * N + (size_t)(g0 + src)];
+            active = !(gg.g0.x == 0.f && gg.g0.y == 0.f && gg.g0.z == 0.f && gg.g0.w == 0.f && gg.g1.x == 0.f &&
+                       gg.g1.y == 0.f && gg.g1.z == 0.f && gg.g2.x == 0.f && gg.g2.y == 0.f && gg.g2.z == 0.f);
         }
-        float ST[2][3]; // Sigma T_i^T
+        if (active) {
+            const float mx_ = gg.g0.x, my_ = gg.g0.y, mxx = gg.g0.z, mxy = gg.g0.w;
+            const float myy = gg.g1.x, ddepth = gg.g1.z;
+            dop = gg.g1.y;
+            const float drgb[3] = {gg.g2.x, gg.g2.y, gg.g2.z};
+            const float Sg[3][3] = {{S6[0], S6[1], S6[2]}, {S6[1], S6[3], S6[4]}, {S6[2], S6[4], S6[5]}};
+            const ViewDesc &V = vsp->v[vi];
+            const float px = V.R[0] * gx + V.R[1] * gy + V.R[2] * gz + V.t[0];
+            const float py = V.R[3] * gx + V.R[4] * gy + V.R[5] * gz + V.t[1];
+            const float pz = V.R[6] * gx + V.R[7] * gy + V.R[8] * gz + V.t[2];
+            const float iz = 1.f / pz;
+            const float xz = px * iz, yz = py * iz;
+            const bool clx = xz < -V.limx || xz > V.limx;
+            const bool cly = yz < -V.limy || yz > V.limy;
+            const float txc = fminf(V.limx, fmaxf(-V.limx, xz));
+            const float tyc = fminf(V.limy, fmaxf(-V.limy, yz));
+            const float J00 = V.fx * iz, J02 = -V.fx * txc * iz;
+            const float J11 = V.fy * iz, J12 = -V.fy * tyc * iz;
+            float T[2][3];
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) {
+                T[0][j] = J00 * V.R[j] + J02 * V.R[6 + j];
+                T[1][j] = J11 * V.R[3 + j] + J12 * V.R[6 + j];
+            }
+            float ST[2][3]; // Sigma T_i^T
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int rr = 0; rr < 3; ++rr)
+                    ST[i][rr] = Sg[rr][0] * T[i][0] + Sg[rr][1] * T[i][1] + Sg[rr][2] * T[i][2];
+            const float a = T[0][0] * ST[0][0] + T[0][1] * ST[0][1] + T[0][2] * ST[0][2] + 0.3f;
+            const float b = T[0][0] * ST[1][0] + T[0][1] * ST[1][1] + T[0][2] * ST[1][2];
+            const float c = T[1][0] * ST[1][0] + T[1][1] * ST[1][1] + T[1][2] * ST[1][2] + 0.3f;
+            const float det = a * c - b * b;
+            const float id = 1.f / det, id2 = id * id;
+            // screen-space gradients from the compositing moments (power =
+            // -(A dx^2 + C dy^2)/2 - B dx dy with the conic (A, B, C) = (c, -b, a) / det)
+            const float cA = c * id, cB = -b * id, cC = a * id;
+            const float du = -(cA * mx_ + cB * my_), dv = -(cC * my_ + cB * mx_);
+            const float dA = -0.5f * mxx, dB = -mxy, dC = -0.5f * myy;
+            // conic (A, B, C) = (c, -b, a) / det
+            const float da = -c * c * id2 * dA + b * c * id2 * dB + (id - a * c * id2) * dC;
+            const float dc = (id - a * c * id2) * dA + a * b * id2 * dB - a * a * id2 * dC;
+            const float db = 2.f * b * c * id2 * dA + (-id - 2.f * b * b * id2) * dB + 2.f * a * b * id2 * dC;
+            // a = T0 Sigma T0^T, b = T0 Sigma T1^T, c = T1 Sigma T1^T
 #pragma unroll
             for (int rr = 0; rr < 3; ++rr)
-                ST[i][rr] = Sg[rr][0] * T[i][0] + Sg[rr][1] * T[i][1] + Sg[rr][2] * T[i][2];
-        const float a = T[0][0] * ST[0][0] + T[0][1] * ST[0][1] + T[0][2] * ST[0][2] + 0.3f;
-        const float b = T[0][0] * ST[1][0] + T[0][1] * ST[1][1] + T[0][2] * ST[1][2];
-        const float c = T[1][0] * ST[1][0] + T[1][1] * ST[1][1] + T[1][2] * ST[1][2] + 0.3f;
-        const float det = a * c - b * b;
-        const float id = 1.f / det, id2 = id * id;
-        // screen-space gradients from the compositing moments (power =
-        // -(A dx^2 + C dy^2)/2 - B dx dy with the conic (A, B, C) = (c, -b, a) / det)
-        const float cA = c * id, cB = -b * id, cC = a * id;
-        const float du = -(cA * mx_ + cB * my_), dv = -(cC * my_ + cB * mx_);
-        const float dA = -0.5f * mxx, dB = -mxy, dC = -0.5f * myy;
-        // conic (A, B, C) = (c, -b, a) / det
-        const float da = -c * c * id2 * dA + b * c * id2 * dB + (id - a * c * id2) * dC;
-        const float dc = (id - a * c * id2) * dA + a * b * id2 * dB - a * a * id2 * dC;
-        const float db = 2.f * b * c * id2 * dA + (-id - 2.f * b * b * id2) * dB + 2.f * a * b * id2 * dC;
-        float *acc_col = &s_acc[0][wbase + src];
-        constexpr int ld = kBwdThreads + 1;
-        // a = T0 Sigma T0^T, b = T0 Sigma T1^T, c = T1 Sigma T1^T
 #pragma unroll
-        for (int rr = 0; rr < 3; ++rr)
+                for (int ss = rr; ss < 3; ++ss) {
+                    float v = da * T[0][rr] * T[0][ss] + dc * T[1][rr] * T[1][ss] +
+                              0.5f * db * (T[0][rr] * T[1][ss] + T[1][rr] * T[0][ss]);
+                    // off-diagonal entries collect both symmetric positions
+                    if (ss != rr) v *= 2.f;
+                    t_sig[rr == 0 ? ss : (rr == 1 ? 2 + ss : 5)] = v;
+                }
+            float dT[2][3];
 #pragma unroll
-            for (int ss = rr; ss < 3; ++ss) {
-                float v = da * T[0][rr] * T[0][ss] + dc * T[1][rr] * T[1][ss] +
-                          0.5f * db * (T[0][rr] * T[1][ss] + T[1][rr] * T[0][ss]);
-                // off-diagonal entries collect both symmetric positions
-                if (ss != rr) v *= 2.f;
-                atomicAdd(acc_col + ld * (3 + (rr == 0 ? ss : (rr == 1 ? 2 + ss : 5))), v);
+            for (int rr = 0; rr < 3; ++rr) {
+                dT[0][rr] = 2.f * da * ST[0][rr] + db * ST[1][rr];
+                dT[1][rr] = db * ST[0][rr] + 2.f * dc * ST[1][rr];
             }
-        float dT[2][3];
+            float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < 3; ++rr) {
-            dT[0][rr] = 2.f * da * ST[0][rr] + db * ST[1][rr];
-            dT[1][rr] = db * ST[0][rr] + 2.f * dc * ST[1][rr];
-        }
-        float dJ00 = 0.f, dJ02 = 0.f, dJ11 = 0.f, dJ12 = 0.f;
+            for (int j = 0; j < 3; ++j) {
+                dJ00 += dT[0][j] * V.R[j];
+                dJ02 += dT[0][j] * V.R[6 + j];
+                dJ11 += dT[1][j] * V.R[3 + j];
+                dJ12 += dT[1][j] * V.R[6 + j];
+            }
+            const float iz2 = iz * iz;
+            float dpx = 0.f, dpy = 0.f, dpz = 0.f;
+            dpz -= (dJ00 * V.fx + dJ11 * V.fy) * iz2;
+            if (clx) {
+                dpz += dJ02 * V.fx * txc * iz2;
+            } else {
+                dpx -= dJ02 * V.fx * iz2;
+                dpz += dJ02 * 2.f * V.fx * px * iz2 * iz;
+            }
+            if (cly) {
+                dpz += dJ12 * V.fy * tyc * iz2;
+            } else {
+                dpy -= dJ12 * V.fy * iz2;
+                dpz += dJ12 * 2.f * V.fy * py * iz2 * iz;
+            }
+            // screen position and depth
+            dpx += du * V.fx * iz;
+            dpy += dv * V.fy * iz;
+            dpz += -(du * V.fx * px + dv * V.fy * py) * iz2 + ddepth;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            dJ00 += dT[0][j] * V.R[j];
-            dJ02 += dT[0][j] * V.R[6 + j];
-            dJ11 += dT[1][j] * V.R[3 + j];
-            dJ12 += dT[1][j] * V.R[6 + j];
-        }
-        const float iz2 = iz * iz;
-        float dpx = 0.f, dpy = 0.f, dpz = 0.f;
-        dpz -= (dJ00 * V.fx + dJ11 * V.fy) * iz2;
-        if (clx) {
-            dpz += dJ02 * V.fx * txc * iz2;
-        } else {
-            dpx -= dJ02 * V.fx * iz2;
-            dpz += dJ02 * 2.f * V.fx * px * iz2 * iz;
-        }
-        if (cly) {
-            dpz += dJ12 * V.fy * tyc * iz2;
-        } else {
-            dpy -= dJ12 * V.fy * iz2;
-            dpz += dJ12 * 2.f * V.fy * py * iz2 * iz;
-        }
-        // screen position and depth
-        dpx += du * V.fx * iz;
-        dpy += dv * V.fy * iz;
-        dpz += -(du * V.fx * px + dv * V.fy * py) * iz2 + ddepth;
-        float dm[3];
+            for (int k = 0; k < 3; ++k) dm[k] = V.R[k] * dpx + V.R[3 + k] * dpy + V.R[6 + k] * dpz;
+            // colour through the SH basis at the view direction
+            float ex = gx - V.campos[0], ey = gy - V.campos[1], ez = gz - V.campos[2];
+            const float len = sqrtf(ex * ex + ey * ey + ez * ez);
+            const float il = 1.f / len;
+            ex *= il;
+            ey *= il;
+            ez *= il;
+            sh_values(deg, ex, ey, ez, Y);
+            const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
+            float w16[16];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) dm[k] = V.R[k] * dpx + V.R[3 + k] * dpy + V.R[6 + k] * dpz;
-        // colour through the SH basis at the view direction
-        float ex = gx - V.campos[0], ey = gy - V.campos[1], ez = gz - V.campos[2];
-        const float len = sqrtf(ex * ex + ey * ey + ez * ez);
-        const float il = 1.f / len;
-        ex *= il;
-        ey *= il;
-        ez *= il;
-        float Y[16];
-        sh_values(deg, ex, ey, ez, Y);
-        const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
-        float w16[16];
-        float m3[3];
+            for (int ch = 0; ch < 3; ++ch) {
+                float raw = 0.5f;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float raw = 0.5f;
+                for (int k = 0; k < 16; ++k)
+                    if (k < nk) raw += Y[k] * shg[3 * k + ch];
+                m3[ch] = raw < 0.f ? 0.f : drgb[ch];
+            }
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nk) raw += Y[k] * shg[3 * k + ch];
-            m3[ch] = raw < 0.f ? 0.f : drgb[ch];
-        }
+            for (int k = 0; k < 16; ++k) {
+                w16[k] = 0.f;
+                if (k < nk) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            w16[k] = 0.f;
-            if (k < nk) {
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    atomicAdd(acc_col + ld * (kAccScalars + 3 * k + ch), Y[k] * m3[ch]);
-                    w16[k] += m3[ch] * shg[3 * k + ch];
+                    for (int ch = 0; ch < 3; ++ch) w16[k] += m3[ch] * shg[3 * k + ch];
                 }
             }
+            const float3 gd = sh_weighted_grad(deg, ex, ey, ez, w16);
+            const float dd = gd.x * ex + gd.y * ey + gd.z * ez;
+            dm[0] += (gd.x - ex * dd) * il;
+            dm[1] += (gd.y - ey * dd) * il;
+            dm[2] += (gd.z - ez * dd) * il;
         }
-        const float3 gd = sh_weighted_grad(deg, ex, ey, ez, w16);
-        const float dd = gd.x * ex + gd.y * ey + gd.z * ez;
-        dm[0] += (gd.x - ex * dd) * il;
-        dm[1] += (gd.y - ey * dd) * il;
-        dm[2] += (gd.z - ez * dd) * il;
+        // Add the terms to the owner's accumulators with plain read-modify-writes:
+        // lanes whose owner also appears at a lower lane of this round wait for
+        // their turn, so no two lanes update one column at once.
+        const unsigned same = __match_any_sync(0xffffffffu, active ? src : 32 + lane);
+        const int turn = __popc(same & ((1u << lane) - 1u));
+        const int turns = __reduce_max_sync(0xffffffffu, (unsigned)turn) + 1;
+        float *acc_col = &s_acc[0][wbase + src];
+        constexpr int ld = kBwdThreads + 1;
+        for (int j = 0; j < turns; ++j) {
+            if (active && turn == j) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) atomicAdd(acc_col + ld * k, dm[k]);
-        atomicAdd(acc_col + ld * 9, dop);
+                for (int k = 0; k < 3; ++k) acc_col[ld * k] += dm[k];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) acc_col[ld * (3 + t)] += t_sig[t];
+                acc_col[ld * 9] += dop;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (k < nk) {
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) acc_col[ld * (kAccScalars + 3 * k + ch)] += Y[k] * m3[ch];
+                    }
+            }
+            __syncwarp();
+        }
     }
     __syncwarp();
 
