@@ -33,11 +33,10 @@ struct RenderState {
     DevBuf recs, tiles, zbits, rects;
     DevBuf inst_a_t, inst_a_v, inst_b_t, inst_b_v;
     DevBuf ranges, final_T, n_contrib, vs_dev, counters;
-    DevBuf n_chunks, chunk_base, n_slots, part_base, pair_tile, part; // list-parallel plan
-    DevBuf pair_k, pair_v, pair_k2, pair_v2, stop_at;                 // chunk-major order
+    DevBuf n_chunks, chunk_base, part_base, pair_tile, part; // list-parallel plan
+    DevBuf pair_k, pair_v, pair_v2, stop_at, plan_aux;       // work orders, stop record
     DevBuf pix_state;                                                 // forward combine scratch
     uint32_t pair_cap = 0, slot_cap = 0;
-    int order_in_alt = 0;
     ViewSet vs{};
     GaussParams P{};
     int64_t m = 0;      // instances of the last eager build
@@ -58,7 +57,7 @@ struct RenderState {
         cp.part = (float *)part.p;
         cp.pair_cap = pair_cap;
         cp.slot_cap = slot_cap;
-        cp.pair_order = (const uint32_t *)(order_in_alt ? pair_v2.p : pair_v.p);
+        cp.pair_order = (const uint32_t *)pair_v.p;
         cp.stop_at = (uint32_t *)stop_at.p;
         return cp;
     }
@@ -197,8 +196,8 @@ void release(lvigs_ctx *ctx, DevBuf &b) {
 void release_state(lvigs_ctx *ctx, RenderState &s) {
     DevBuf *all[] = {&s.recs, &s.tiles, &s.zbits, &s.rects, &s.inst_a_t, &s.inst_a_v, &s.inst_b_t,
                      &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters,
-                     &s.n_chunks, &s.chunk_base, &s.n_slots, &s.part_base, &s.pair_tile, &s.part,
-                     &s.pair_k, &s.pair_v, &s.pair_k2, &s.pair_v2, &s.stop_at, &s.pix_state};
+                     &s.n_chunks, &s.chunk_base, &s.part_base, &s.pair_tile, &s.part,
+                     &s.pair_k, &s.pair_v, &s.pair_v2, &s.stop_at, &s.plan_aux, &s.pix_state};
     for (DevBuf *b : all) release(ctx, *b);
     s.valid = false;
     s.m_cap = 0;
@@ -321,9 +320,9 @@ lvigs_status ensure_plan(lvigs_ctx *ctx, RenderState &st) {
     LV_TRY(ensure(ctx, st.pair_tile, (size_t)pairs * 4));
     LV_TRY(ensure(ctx, st.pair_k, (size_t)pairs * 4));
     LV_TRY(ensure(ctx, st.pair_v, (size_t)pairs * 4));
-    LV_TRY(ensure(ctx, st.pair_k2, (size_t)pairs * 4));
     LV_TRY(ensure(ctx, st.pair_v2, (size_t)pairs * 4));
     LV_TRY(ensure(ctx, st.stop_at, (size_t)st.vs.total_pixels * 4));
+    LV_TRY(ensure(ctx, st.plan_aux, plan_aux_bytes(st.vs.total_tiles)));
     LV_TRY(ensure(ctx, st.pix_state, (size_t)st.vs.total_pixels * pix_state_bytes()));
     LV_TRY(ensure(ctx, st.part, (size_t)slots * chunk_slot_bytes(st.vs.tile_w, st.vs.tile_h)));
     st.pair_cap = (uint32_t)pairs;
@@ -335,7 +334,8 @@ lvigs_status ensure_plan(lvigs_ctx *ctx, RenderState &st) {
 // emit, tile sort, ranges.  In eager mode the call waits once to learn the
 // instance count and grows the instance buffers; otherwise it relies on
 // st.m_cap (overflow is latched in the status word).
-lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool eager, double headroom) {
+lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool eager, double headroom,
+                         GGrad *g2d_init = nullptr) {
     const int64_t N = st.P.n;
     const int64_t VN = N * st.vs.n_views;
     LV_TRY(ensure(ctx, st.recs, (size_t)VN * sizeof(GRec)));
@@ -346,7 +346,6 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     LV_TRY(ensure(ctx, st.ranges, (size_t)st.vs.total_tiles * sizeof(uint2)));
     LV_TRY(ensure(ctx, st.n_chunks, (size_t)st.vs.total_tiles * 4));
     LV_TRY(ensure(ctx, st.chunk_base, (size_t)st.vs.total_tiles * 4));
-    LV_TRY(ensure(ctx, st.n_slots, (size_t)st.vs.total_tiles * 4));
     LV_TRY(ensure(ctx, st.part_base, (size_t)st.vs.total_tiles * 4));
     LV_TRY(ensure(ctx, ctx->pos, (size_t)VN * 4));
     LV_TRY(ensure(ctx, ctx->ck, (size_t)VN * 4));
@@ -371,7 +370,7 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     {
         Phase ph(ctx, LVIGS_PHASE_PREPROCESS, s);
         launch_preprocess_fwd(st.P, vsd, (GRec *)st.recs.p, (uint32_t *)st.tiles.p, (uint32_t *)st.zbits.p,
-                              (uint2 *)st.rects.p, s);
+                              (uint2 *)st.rects.p, g2d_init, s);
     }
     {
         Phase ph(ctx, LVIGS_PHASE_COMPACT, s);
@@ -419,19 +418,10 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     {
         Phase ph(ctx, LVIGS_PHASE_RANGES, s);
         launch_ranges(st.sorted_tiles(), cnt + 2, st.m_cap, (uint2 *)st.ranges.p, st.vs.total_tiles, s);
-        // list-parallel plan: chunks per tile, pair and slot numbering
-        launch_chunk_counts((const uint2 *)st.ranges.p, st.vs.total_tiles, kChunkLen, (uint32_t *)st.n_chunks.p,
-                            (uint32_t *)st.n_slots.p, s);
-        launch_scan((const uint32_t *)st.n_chunks.p, nullptr, 0, (uint32_t *)st.chunk_base.p, cnt + 4, nullptr,
-                    st.vs.total_tiles, (uint32_t *)ctx->scan_tmp.p, s);
-        launch_scan((const uint32_t *)st.n_slots.p, nullptr, 0, (uint32_t *)st.part_base.p, cnt + 5, nullptr,
-                    st.vs.total_tiles, (uint32_t *)ctx->scan_tmp.p, s);
-        launch_chunk_pairs(st.plan(), st.vs.total_tiles, (uint32_t *)ctx->status.p, s);
-        // chunk-major work order (stable by pair) and the per-pixel stop record
-        launch_pair_keys(st.plan(), st.vs.total_tiles, (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
-        st.order_in_alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p,
-                                            (uint32_t *)st.pair_k2.p, (uint32_t *)st.pair_v2.p, cnt + 4,
-                                            st.pair_cap, 8, (uint32_t *)ctx->radix_tmp.p, s);
+        // list-parallel plan: chunks per tile, pair and slot numbering, the
+        // chunk-major work order; and the per-pixel stop record
+        launch_plan(st.plan(), (const uint2 *)st.ranges.p, st.vs.total_tiles, cnt, (uint32_t *)st.pair_v.p,
+                    (uint32_t *)st.plan_aux.p, (uint32_t *)ctx->status.p, s);
         LV_CUDA(cudaMemsetAsync(st.stop_at.p, 0xff, (size_t)st.vs.total_pixels * 4, s));
     }
     return LVIGS_OK;
@@ -443,11 +433,10 @@ ChunkPlan backward_plan(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
     ChunkPlan cp = st.plan();
     uint32_t *cnt = (uint32_t *)st.counters.p;
     launch_bwd_pair_keys(st.vs, (const ViewSet *)st.vs_dev.p, cp, (const int32_t *)st.n_contrib.p,
-                         (uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, s);
-    const int alt = launch_radix_sort((uint32_t *)st.pair_k.p, (uint32_t *)st.pair_v.p, (uint32_t *)st.pair_k2.p,
-                                      (uint32_t *)st.pair_v2.p, cnt + 4, st.pair_cap, 8,
-                                      (uint32_t *)ctx->radix_tmp.p, s);
-    cp.pair_order = (const uint32_t *)(alt ? st.pair_v2.p : st.pair_v.p);
+                         (uint32_t *)st.pair_k.p, (uint32_t *)st.plan_aux.p, s);
+    launch_bucket_place((const uint32_t *)st.pair_k.p, cnt + 4, st.pair_cap, (uint32_t *)st.plan_aux.p,
+                        (uint32_t *)st.pair_v2.p, s);
+    cp.pair_order = (const uint32_t *)st.pair_v2.p;
     return cp;
 }
 
@@ -913,8 +902,12 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         Phase ph(ctx, LVIGS_PHASE_PYRAMID, s);
         for (int l = 1; l <= LVIGS_MAX_LEVEL; ++l) launch_pyramid_views(pv[l], l, s);
     }
-    // 2. a1-a4 over all views at once
-    LV_TRY(build_lists(ctx, st, s, eager, 1.3));
+    // 2. a1-a4 over all views at once; preprocessing also clears the gradient
+    // records of the pairs the backward will read (forward and backward of one
+    // call, so nothing else writes them in between)
+    const int64_t VN = (int64_t)st.P.n * V;
+    LV_TRY(ensure(ctx, ctx->g2d, (size_t)VN * sizeof(GGrad)));
+    LV_TRY(build_lists(ctx, st, s, eager, 1.3, (GGrad *)ctx->g2d.p));
     // 3. a5 into the caller's images or the internal ones
     const size_t TP = st.vs.total_pixels;
     LV_TRY(ensure(ctx, st.final_T, TP * 4));
@@ -970,9 +963,6 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         launch_loss(lv, ctx->loss_tmp.p, s);
     }
     // 5. a6 + a7
-    const int64_t VN = (int64_t)st.P.n * V;
-    LV_TRY(ensure(ctx, ctx->g2d, (size_t)VN * sizeof(GGrad)));
-    if (VN > 0) LV_CUDA(cudaMemsetAsync(ctx->g2d.p, 0, (size_t)VN * sizeof(GGrad), s));
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
         const ChunkPlan bp = backward_plan(ctx, st, s);

@@ -872,45 +872,190 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     }
 }
 
-// Chunk plan: chunks per tile, and for multi-chunk tiles the number of slots.
-__global__ void chunk_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L,
-                                   uint32_t *__restrict__ n_chunks, uint32_t *__restrict__ n_slots) {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+// List-parallel plan: per tile the number of chunks (an empty tile still has
+// one), its first pair and, for a multi-chunk tile, its first slot (exclusive
+// scans over the tiles), the tile of every pair, and the forward work order:
+// pairs by chunk index, all first chunks (in tile order), then all second
+// chunks, ... (chunks from the 255th on share the last bucket).  Within a
+// later bucket the order is that of arrival, which only schedules work: no
+// result depends on it.
+//
+// Two launches over the tiles, one thread per tile.  The first counts and
+// publishes per-block sums and bucket counts; the block that finishes last (a
+// ticket taken after a fence, no waiting) turns them into block bases and
+// bucket start positions.  The second places every pair.
+//
+// aux (zeroed before the first launch): [0, 256) bucket counts, then start
+// positions, then cursors; [256] the ticket; from 257 two words per block:
+// the block's sums, then its bases.
+constexpr int kPlanThreads = 256;
+constexpr uint32_t kOrderBuckets = 256;
+constexpr int kAuxTicket = 256, kAuxBlocks = 257;
+
+// Exclusive scan of two values over a kPlanThreads block: prefixes returned in
+// a, b; block totals in ta, tb (every thread).
+__device__ __forceinline__ void block_scan2(uint32_t &a, uint32_t &b, uint32_t &ta, uint32_t &tb) {
+    __shared__ uint32_t sa[kPlanThreads / 32], sb[kPlanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) {
+            ia += ya;
+            ib += yb;
+        }
+    }
+    if (lane == 31) {
+        sa[wid] = ia;
+        sb[wid] = ib;
+    }
+    __syncthreads();
+    uint32_t wa = 0, wb = 0;
+    ta = tb = 0;
+#pragma unroll
+    for (int j = 0; j < kPlanThreads / 32; ++j) {
+        if (j < wid) {
+            wa += sa[j];
+            wb += sb[j];
+        }
+        ta += sa[j];
+        tb += sb[j];
+    }
+    __syncthreads(); // sa, sb reusable
+    a = wa + ia - a;
+    b = wb + ib - b;
+}
+
+// In the last block: exclusive scan of the 256 bucket counts in aux, in
+// place (written by other blocks' atomics: read from L2).
+__device__ __forceinline__ void bucket_starts(uint32_t *aux) {
+    __shared__ uint32_t sv[kOrderBuckets];
+    for (uint32_t i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) sv[i] = __ldcg(aux + i);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        constexpr int per = kOrderBuckets / 32;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < per; ++j) sum += sv[lane * per + j];
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int j = 0; j < per; ++j) {
+            const uint32_t v = sv[lane * per + j];
+            aux[lane * per + j] = run;
+            run += v;
+        }
+    }
+}
+
+// True in every thread of the block that finished last (after its own
+// published results); the other blocks' writes are then visible to it.
+__device__ __forceinline__ bool last_block(uint32_t *ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+plan_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L, uint32_t *__restrict__ n_chunks,
+                  uint32_t *__restrict__ aux, uint32_t *__restrict__ counters) {
+    __shared__ uint32_t hist[kOrderBuckets];
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < kOrderBuckets; i += kPlanThreads) hist[i] = 0;
+    __syncthreads();
+    const uint32_t t = blockIdx.x * kPlanThreads + tid;
+    uint32_t c = 0;
+    if (t < n_tiles) {
         const uint2 r = ranges[t];
         const uint32_t len = r.y - r.x;
-        const uint32_t c = len > L ? (len + L - 1) / L : 1u;
+        c = len > L ? (len + L - 1) / L : 1u;
         n_chunks[t] = c;
-        n_slots[t] = c > 1 ? c : 0u;
+        // bucket k > 0 counts the tiles with more than k chunks
+        const uint32_t kc = min(c, kOrderBuckets - 1);
+        for (uint32_t k = 1; k < kc; ++k) atomicAdd(&hist[k], 1u);
+        if (c > kc) atomicAdd(&hist[kOrderBuckets - 1], c - kc);
     }
-}
-
-__global__ void chunk_pairs_kernel(const uint32_t *__restrict__ n_chunks, const uint32_t *__restrict__ chunk_base,
-                                   const uint32_t *__restrict__ part_base, uint32_t n_tiles,
-                                   uint32_t *__restrict__ pair_tile, uint32_t pair_cap, uint32_t slot_cap,
-                                   uint32_t *status) {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
-        const uint32_t c = n_chunks[t], b = chunk_base[t];
-        if (c > 1 && part_base[t] + c > slot_cap) atomicOr(status, kStatusCapacity);
-        if (b + c > pair_cap) {
-            atomicOr(status, kStatusCapacity);
-            continue;
+    uint32_t a = c, b = c > 1 ? c : 0u, ta, tb;
+    block_scan2(a, b, ta, tb); // (synchronises: hist is complete)
+    for (uint32_t i = tid; i < kOrderBuckets; i += kPlanThreads)
+        if (hist[i]) atomicAdd(aux + i, hist[i]);
+    if (tid == 0) {
+        aux[kAuxBlocks + 2 * blockIdx.x] = ta;
+        aux[kAuxBlocks + 2 * blockIdx.x + 1] = tb;
+    }
+    if (!last_block(aux + kAuxTicket)) return;
+    // block bases (exclusive scan of the block sums), in chunks of the block size
+    uint32_t carry_a = 0, carry_b = 0;
+    for (uint32_t b0 = 0; b0 < gridDim.x; b0 += kPlanThreads) {
+        const uint32_t j = b0 + tid;
+        uint32_t sa = 0, sb = 0;
+        if (j < gridDim.x) {
+            sa = __ldcg(aux + kAuxBlocks + 2 * j);
+            sb = __ldcg(aux + kAuxBlocks + 2 * j + 1);
         }
-        for (uint32_t k = 0; k < c; ++k) pair_tile[b + k] = t;
+        uint32_t ea = sa, eb = sb, tot_a, tot_b;
+        block_scan2(ea, eb, tot_a, tot_b);
+        if (j < gridDim.x) {
+            aux[kAuxBlocks + 2 * j] = carry_a + ea;
+            aux[kAuxBlocks + 2 * j + 1] = carry_b + eb;
+        }
+        carry_a += tot_a;
+        carry_b += tot_b;
+    }
+    if (tid == 0) {
+        counters[4] = carry_a; // pairs
+        counters[5] = carry_b; // slots
+        aux[0] = n_tiles;      // bucket 0: the first chunks
+    }
+    __syncthreads();
+    bucket_starts(aux);
+}
+
+__global__ void __launch_bounds__(kPlanThreads)
+plan_place_kernel(uint32_t n_tiles, const uint32_t *__restrict__ n_chunks, uint32_t *__restrict__ chunk_base,
+                  uint32_t *__restrict__ part_base, uint32_t *__restrict__ pair_tile, uint32_t pair_cap,
+                  uint32_t slot_cap, uint32_t *__restrict__ order, uint32_t *__restrict__ aux, uint32_t *status) {
+    const uint32_t t = blockIdx.x * kPlanThreads + threadIdx.x;
+    const uint32_t c = t < n_tiles ? n_chunks[t] : 0u;
+    uint32_t cb = c, pb = c > 1 ? c : 0u, ta, tb;
+    block_scan2(cb, pb, ta, tb);
+    if (t >= n_tiles) return;
+    cb += aux[kAuxBlocks + 2 * blockIdx.x];
+    pb += aux[kAuxBlocks + 2 * blockIdx.x + 1];
+    chunk_base[t] = cb;
+    part_base[t] = pb;
+    if (c > 1 && pb + c > slot_cap) atomicOr(status, kStatusCapacity);
+    if (cb + c > pair_cap) {
+        atomicOr(status, kStatusCapacity);
+        return;
+    }
+    for (uint32_t k = 0; k < c; ++k) pair_tile[cb + k] = t;
+    order[t] = cb;
+    for (uint32_t k = 1; k < c; ++k) {
+        const uint32_t pos = atomicAdd(aux + min(k, kOrderBuckets - 1), 1u);
+        if (pos < pair_cap) order[pos] = cb + k;
     }
 }
 
-// Sort keys for chunk-major work order: the chunk index of every pair.
-__global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const uint32_t *__restrict__ chunk_base,
-                                 const uint32_t *n_pairs, uint32_t pair_cap, uint32_t n_tiles,
-                                 uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    const uint32_t n = min(*n_pairs, pair_cap);
+// Backward work order from the 8-bit keys: pos = next free position of the
+// pair's bucket (start positions in aux from the keys kernel).
+__global__ void bucket_place_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, uint32_t cap,
+                                    uint32_t *__restrict__ aux, uint32_t *__restrict__ order) {
+    const uint32_t n = min(*n_dev, cap);
     for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        // 8-bit keys (one radix pass): chunks from the 255th on share the last
-        // bucket, in pair order; the order only schedules work
-        const uint32_t t = pair_tile[p];
-        const uint32_t k = t < n_tiles ? p - chunk_base[t] : 255u;
-        keys[p] = k < 255u ? k : 255u;
-        vals[p] = p;
+        const uint32_t pos = atomicAdd(aux + (keys[p] & (kOrderBuckets - 1)), 1u);
+        if (pos < n) order[pos] = p;
     }
 }
 
@@ -918,11 +1063,11 @@ __global__ void pair_keys_kernel(const uint32_t *__restrict__ pair_tile, const u
 // part of the chunk before the tile's furthest last contributor; the longest
 // items start first, which keeps the tail of the persistent kernel short.
 // One warp per pair; key = (L - walk) scaled to 0..254 (0 first), 255 for
-// pairs of no tile: 8 bits, one radix pass.
+// pairs of no tile: 8 bits, one bucket pass.
 template <int TW, int TH>
 __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp,
                                      const int32_t *__restrict__ n_contrib, uint32_t *__restrict__ keys,
-                                     uint32_t *__restrict__ vals) {
+                                     uint32_t *__restrict__ aux) {
     using Gm = Geometry<TW, TH>;
     const uint32_t n = min(*cp.n_pairs, cp.pair_cap);
     const int lane = threadIdx.x & 31;
@@ -947,9 +1092,10 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
         }
         if (lane == 0) {
             keys[p] = key;
-            vals[p] = p;
+            atomicAdd(aux + key, 1u);
         }
     }
+    if (last_block(aux + kAuxTicket)) bucket_starts(aux);
 }
 
 template <typename K>
@@ -1027,40 +1173,45 @@ void bwd_dispatch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, co
 
 } // namespace
 
-void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t *n_chunks, uint32_t *n_slots,
+size_t plan_aux_bytes(uint32_t n_tiles) {
+    return sizeof(uint32_t) * (kAuxBlocks + 2 * (size_t)((n_tiles + kPlanThreads - 1) / kPlanThreads));
+}
+
+void launch_plan(const ChunkPlan &cp, const uint2 *ranges, uint32_t n_tiles, uint32_t *counters, uint32_t *order,
+                 uint32_t *aux, uint32_t *status, cudaStream_t s) {
+    if (n_tiles == 0) {
+        cudaMemsetAsync(counters + 4, 0, 2 * sizeof(uint32_t), s);
+        return;
+    }
+    const unsigned nb = (n_tiles + kPlanThreads - 1) / kPlanThreads;
+    cudaMemsetAsync(aux, 0, sizeof(uint32_t) * kAuxBlocks, s);
+    plan_count_kernel<<<nb, kPlanThreads, 0, s>>>(ranges, n_tiles, (uint32_t)cp.L, (uint32_t *)cp.n_chunks, aux,
+                                                  counters);
+    plan_place_kernel<<<nb, kPlanThreads, 0, s>>>(n_tiles, cp.n_chunks, (uint32_t *)cp.chunk_base,
+                                                  (uint32_t *)cp.part_base, (uint32_t *)cp.pair_tile, cp.pair_cap,
+                                                  cp.slot_cap, order, aux, status);
+}
+
+void launch_bucket_place(const uint32_t *keys, const uint32_t *n_dev, uint32_t cap, uint32_t *aux, uint32_t *order,
                          cudaStream_t s) {
-    if (n_tiles == 0) return;
-    int blocks = (int)((n_tiles + 255) / 256);
+    if (cap == 0) return;
+    int blocks = (int)((cap + 255) / 256);
     if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
-    chunk_count_kernel<<<blocks, 256, 0, s>>>(ranges, n_tiles, (uint32_t)L, n_chunks, n_slots);
-}
-
-void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s) {
-    if (n_tiles == 0) return;
-    int blocks = (int)((n_tiles + 255) / 256);
-    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
-    chunk_pairs_kernel<<<blocks, 256, 0, s>>>(cp.n_chunks, cp.chunk_base, cp.part_base, n_tiles,
-                                              (uint32_t *)cp.pair_tile, cp.pair_cap, cp.slot_cap, status);
-}
-
-void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s) {
-    if (cp.pair_cap == 0) return;
-    int blocks = (int)((cp.pair_cap + 255) / 256);
-    if (blocks > device_sm_count() * 8) blocks = device_sm_count() * 8;
-    pair_keys_kernel<<<blocks, 256, 0, s>>>(cp.pair_tile, cp.chunk_base, cp.n_pairs, cp.pair_cap, n_tiles, keys, vals);
+    bucket_place_kernel<<<blocks, 256, 0, s>>>(keys, n_dev, cap, aux, order);
 }
 
 void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan &cp, const int32_t *n_contrib,
-                          uint32_t *keys, uint32_t *vals, cudaStream_t s) {
+                          uint32_t *keys, uint32_t *aux, cudaStream_t s) {
     if (cp.pair_cap == 0) return;
+    cudaMemsetAsync(aux, 0, sizeof(uint32_t) * kAuxBlocks, s);
     uint64_t blocks = ((uint64_t)cp.pair_cap * 32 + 255) / 256;
     if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
     if (vs.tile_w == 16 && vs.tile_h == 16)
-        bwd_pair_keys_kernel<16, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
+        bwd_pair_keys_kernel<16, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, aux);
     else if (vs.tile_w == 8 && vs.tile_h == 8)
-        bwd_pair_keys_kernel<8, 8><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
+        bwd_pair_keys_kernel<8, 8><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, aux);
     else if (vs.tile_w == 32 && vs.tile_h == 16)
-        bwd_pair_keys_kernel<32, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, vals);
+        bwd_pair_keys_kernel<32, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, aux);
 }
 
 size_t chunk_slot_bytes(int tile_w, int tile_h) {

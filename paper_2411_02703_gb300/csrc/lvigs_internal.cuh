@@ -76,13 +76,17 @@ struct __align__(16) GRec {
 // Screen-space gradient sums of one (view, Gaussian) over its pixels, with
 // dp = dL/dpower and (dx, dy) = (u - px, v - py):
 // g0 = (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy),
-// g1 = (sum dp dy^2, dL/dopacity, dL/dz, -), g2 = (dL/dr, dL/dg, dL/db, -).
+// g1 = (sum dp dy^2, dL/dopacity, dL/dz, -), g2 = (dL/dr, dL/dg, dL/db, clamp
+// word).  The clamp word is the bit pattern kClampKnown | (bit c set when colour
+// channel c was clamped at 0) when forward preprocessing cleared the record,
+// else 0 (the backward preprocessing then re-evaluates the colour).
 // Since power = -(A dx^2 + C dy^2)/2 - B dx dy, the conic gradients follow per
 // Gaussian: dL/du = -(A m_x + B m_y), dL/dv = -(C m_y + B m_x),
 // dL/dA = -m_xx / 2, dL/dB = -m_xy, dL/dC = -m_yy / 2.
 struct __align__(16) GGrad {
     float4 g0, g1, g2;
 };
+constexpr uint32_t kClampKnown = 0x40000000u;
 
 __host__ __device__ inline int view_of_tile(const ViewSet &vs, uint32_t gt) {
     int v = 0;
@@ -159,8 +163,10 @@ struct ExpKeyTable {
 // y[i] = (float)exp((double)x[i]) as the key stage evaluates it (parity hook).
 void launch_exp_key(const float *x, float *y, int64_t n, cudaStream_t s);
 
+// g2d_init (may be null): the per-pair gradient records of the backward, cleared
+// here for every pair that has tiles, with its colour clamp word.
 void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs_dev, GRec *recs, uint32_t *tiles,
-                           uint32_t *zbits, uint2 *rects, cudaStream_t s);
+                           uint32_t *zbits, uint2 *rects, GGrad *g2d_init, cudaStream_t s);
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs_dev, const uint32_t *tiles,
                            const GGrad *g2d, const ParamGrads &G, cudaStream_t s);
 
@@ -213,14 +219,21 @@ struct ChunkPlan {
     const uint32_t *pair_order; // [pair_cap] work order (chunk-major), or null
     uint32_t *stop_at;          // [total pixels] first chunk with a local stop (reset to ~0)
 };
-void launch_chunk_counts(const uint2 *ranges, uint32_t n_tiles, int L, uint32_t *n_chunks, uint32_t *n_slots,
+// The plan from the tile ranges: n_chunks, chunk_base, part_base and
+// pair_tile of cp, counters[4] = pairs, counters[5] = slots, and the
+// chunk-major forward work order in `order`; capacity overflow is latched.
+// aux: plan_aux_bytes(n_tiles) of scratch.
+size_t plan_aux_bytes(uint32_t n_tiles);
+void launch_plan(const ChunkPlan &cp, const uint2 *ranges, uint32_t n_tiles, uint32_t *counters, uint32_t *order,
+                 uint32_t *aux, uint32_t *status, cudaStream_t s);
+// order[0, n) = the pairs by the 8-bit keys of launch_bwd_pair_keys (n =
+// min(*n_dev, cap)), with the bucket starts it left in aux.
+void launch_bucket_place(const uint32_t *keys, const uint32_t *n_dev, uint32_t cap, uint32_t *aux, uint32_t *order,
                          cudaStream_t s);
-void launch_chunk_pairs(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *status, cudaStream_t s);
-void launch_pair_keys(const ChunkPlan &cp, uint32_t n_tiles, uint32_t *keys, uint32_t *vals, cudaStream_t s);
 size_t chunk_slot_bytes(int tile_w, int tile_h);
-// Keys of the backward work order (11 bits: L - expected walk of each pair).
+// Keys of the backward work order (8 bits: L - expected walk of each pair).
 void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan &cp, const int32_t *n_contrib,
-                          uint32_t *keys, uint32_t *vals, cudaStream_t s);
+                          uint32_t *keys, uint32_t *aux, cudaStream_t s);
 
 // Compositing: persistent warps, one (tile, chunk, 8x8 block) per work item;
 // each stages 32 * bm Gaussians per round (bm = 1 or 2).  `queue` is one device

@@ -238,9 +238,13 @@ constexpr int kShPitch = 49; // staged row pitch: odd, so lanes reading 32 rows 
 
 // A warp's 32 consecutive SH rows (one contiguous run of nrows * row floats)
 // into dst at pitch kShPitch: float4 loads all issued before the stores when
-// the run is 16-byte aligned.  row <= kShRow.
-__device__ __forceinline__ void stage_sh_rows(const float *__restrict__ src, int nrows, int row, int lane,
-                                              float *__restrict__ dst) {
+// the run is 16-byte aligned.  ROW is the row length when known at compile
+// time (the degree-3 row; the element's row then comes from a constant
+// divide), else 0 and `row` gives it.  row <= kShRow.
+template <int ROW>
+__device__ __forceinline__ void stage_sh_rows_t(const float *__restrict__ src, int nrows, int row, int lane,
+                                                float *__restrict__ dst) {
+    if (ROW) row = ROW;
     const int n = nrows * row;
     if ((((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
         constexpr int kMaxIt = 32 * kShRow / 4 / 32;
@@ -268,6 +272,12 @@ __device__ __forceinline__ void stage_sh_rows(const float *__restrict__ src, int
             dst[rr * kShPitch + cc] = __ldg(src + e);
         }
     }
+}
+
+__device__ __forceinline__ void stage_sh_rows(const float *__restrict__ src, int nrows, int row, int lane,
+                                              float *__restrict__ dst) {
+    if (row == kShRow) stage_sh_rows_t<kShRow>(src, nrows, row, lane, dst);
+    else stage_sh_rows_t<0>(src, nrows, row, lane, dst);
 }
 
 // mu_I = [Q_iw, T_iw] mu_W (Eq. 7), strict binary32.
@@ -298,7 +308,7 @@ constexpr int kFwdThreads = 128;
 __global__ void __launch_bounds__(kFwdThreads)
 preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__restrict__ recs,
                       uint32_t *__restrict__ tiles, uint32_t *__restrict__ zbits,
-                      uint2 *__restrict__ rects, ExpKeyTable et_param) {
+                      uint2 *__restrict__ rects, GGrad *__restrict__ g2d_init, ExpKeyTable et_param) {
     __shared__ float s_sh[kFwdThreads / 32][32 * kShPitch];
     __shared__ ExpKeyTable et;
     if (threadIdx.x < 32) {
@@ -457,13 +467,19 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
         sh_values(deg, dx, dy, dz, Y);
         const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
         float rgb[3];
+        uint32_t clamp = kClampKnown;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.5f;
 #pragma unroll
             for (int k = 0; k < 16; ++k)
                 if (k < nk) acc += Y[k] * shg[3 * k + ch];
+            if (acc < 0.f) clamp |= 1u << ch;
             rgb[ch] = fmaxf(acc, 0.f);
+        }
+        if (g2d_init) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            g2d_init[o] = GGrad{z, z, make_float4(0.f, 0.f, 0.f, __uint_as_float(clamp))};
         }
         // half-extents of the box where o exp(power) can reach 1/255: the
         // ellipse d^T Sigma_I^{-1} d <= 2 (ln(255 o) + 0.1), widened by 0.05 px;
@@ -506,6 +522,59 @@ constexpr int kAccScalars = 10; // d_mean 3, dSigma 6 (00,01,02,11,12,22), d_opa
 constexpr size_t kBwdSmem = sizeof(float) * ((kAccScalars + kShRow) * (kBwdThreads + 1) + kBwdThreads * kShPitch) +
                             sizeof(uint32_t) * (kBwdThreads / 32) * kMaxViews +
                             sizeof(int) * (kBwdThreads / 32) * (kMaxViews + 1);
+
+// Rows [0, nrows) of the warp's SH gradients from the accumulators (column
+// wbase + row, one accumulator row per coefficient-channel at pitch ld) to
+// dst, consecutive lanes on consecutive floats; columns from `live` on are
+// zero (left as they are when accumulating).  ROW as in stage_sh_rows_t; with
+// ROW and a 16-byte aligned dst the run moves as float4, and when
+// accumulating every load of a lane is issued before its first store.
+template <int ROW>
+__device__ __forceinline__ void write_sh_grad_rows(float *__restrict__ dst, int nrows, int row, int live_cols,
+                                                   const float *__restrict__ acc, int ld, int wbase, int lane,
+                                                   int accumulate) {
+    if (ROW) row = ROW;
+    const int n = nrows * row;
+    if (ROW && (ROW & 3) == 0 && (((uintptr_t)dst) & 15u) == 0) {
+        constexpr int kIt = 32 * (ROW ? ROW : 4) / 4 / 32;
+        float4 old[kIt];
+        if (accumulate) {
+#pragma unroll
+            for (int i = 0; i < kIt; ++i) {
+                const int e4 = lane + 32 * i;
+                if (4 * e4 < n) old[i] = reinterpret_cast<const float4 *>(dst)[e4];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kIt; ++i) {
+            const int e = 4 * (lane + 32 * i);
+            if (e >= n) continue;
+            float v[4], o[4] = {0.f, 0.f, 0.f, 0.f};
+            if (accumulate) {
+                o[0] = old[i].x;
+                o[1] = old[i].y;
+                o[2] = old[i].z;
+                o[3] = old[i].w;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int rw = (e + c) / ROW, col = (e + c) - rw * ROW;
+                const bool live = col < live_cols && col < kShRow;
+                v[c] = live ? (accumulate ? o[c] + acc[col * ld + wbase + rw] : acc[col * ld + wbase + rw])
+                            : (accumulate ? o[c] : 0.f);
+            }
+            reinterpret_cast<float4 *>(dst)[e / 4] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+        return;
+    }
+    for (int e = lane; e < n; e += 32) {
+        const int rw = e / row, col = e - rw * row;
+        const bool live = col < live_cols && col < kShRow;
+        const float v = live ? acc[col * ld + wbase + rw] : 0.f;
+        if (!accumulate) dst[e] = v;
+        else if (live) dst[e] += v;
+    }
+}
 
 __global__ void __launch_bounds__(kBwdThreads, 4)
 preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint32_t *__restrict__ tiles,
@@ -725,13 +794,21 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
             sh_values(deg, ex, ey, ez, Y);
             const float *shg = staged ? &s_sh[w][src * kShPitch] : P.sh + (size_t)(g0 + src) * row;
             float w16[16];
+            // colour channels clamped at 0 pass no gradient: from the clamp word
+            // the forward left in the record, else from the colour re-evaluated
+            const uint32_t clamp = __float_as_uint(gg.g2.w);
+            if (clamp & kClampKnown) {
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float raw = 0.5f;
+                for (int ch = 0; ch < 3; ++ch) m3[ch] = (clamp >> ch) & 1u ? 0.f : drgb[ch];
+            } else {
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (k < nk) raw += Y[k] * shg[3 * k + ch];
-                m3[ch] = raw < 0.f ? 0.f : drgb[ch];
+                for (int ch = 0; ch < 3; ++ch) {
+                    float raw = 0.5f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < nk) raw += Y[k] * shg[3 * k + ch];
+                    m3[ch] = raw < 0.f ? 0.f : drgb[ch];
+                }
             }
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
@@ -854,13 +931,10 @@ preprocess_bwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, const uint
     // SH gradient rows of the warp's Gaussians, contiguous in memory: written
     // with consecutive lanes on consecutive floats
     float *dst = G.d_sh + g0 * row;
-    for (int e = lane; e < nrows * row; e += 32) {
-        const int rw = e / row, col = e - rw * row;
-        const bool live = col < 3 * nk && col < kShRow;
-        const float v = live ? s_acc[kAccScalars + col][wbase + rw] : 0.f;
-        if (!G.accumulate) dst[e] = v;
-        else if (live) dst[e] += v;
-    }
+    if (row == kShRow) write_sh_grad_rows<kShRow>(dst, nrows, row, 3 * nk, s_acc[kAccScalars], kBwdThreads + 1,
+                                                  wbase, lane, G.accumulate);
+    else write_sh_grad_rows<0>(dst, nrows, row, 3 * nk, s_acc[kAccScalars], kBwdThreads + 1, wbase, lane,
+                               G.accumulate);
 }
 
 __global__ void exp_key_kernel(const float *__restrict__ x, float *__restrict__ y, int64_t n, ExpKeyTable t) {
@@ -905,10 +979,11 @@ void launch_exp_key(const float *x, float *y, int64_t n, cudaStream_t s) {
 }
 
 void launch_preprocess_fwd(const GaussParams &P, const ViewSet *vs, GRec *recs, uint32_t *tiles,
-                           uint32_t *zbits, uint2 *rects, cudaStream_t s) {
+                           uint32_t *zbits, uint2 *rects, GGrad *g2d_init, cudaStream_t s) {
     if (P.n <= 0) return;
     const int blocks = (P.n + kFwdThreads - 1) / kFwdThreads;
-    preprocess_fwd_kernel<<<blocks, kFwdThreads, 0, s>>>(P, vs, recs, tiles, zbits, rects, exp_key_table());
+    preprocess_fwd_kernel<<<blocks, kFwdThreads, 0, s>>>(P, vs, recs, tiles, zbits, rects, g2d_init,
+                                                         exp_key_table());
 }
 
 void launch_preprocess_bwd(const GaussParams &P, const ViewSet *vs, const uint32_t *tiles,
