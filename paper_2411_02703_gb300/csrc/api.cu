@@ -35,6 +35,7 @@ struct RenderState {
     DevBuf ranges, final_T, n_contrib, vs_dev, counters;
     DevBuf n_chunks, chunk_base, part_base, pair_tile, part; // list-parallel plan
     DevBuf pair_k, pair_v, pair_v2, stop_at, plan_aux;       // work orders, stop record
+    DevBuf stop_items;                                       // forward stop walks
     DevBuf pix_state;                                                 // forward combine scratch
     uint32_t pair_cap = 0, slot_cap = 0;
     ViewSet vs{};
@@ -59,6 +60,8 @@ struct RenderState {
         cp.slot_cap = slot_cap;
         cp.pair_order = (const uint32_t *)pair_v.p;
         cp.stop_at = (uint32_t *)stop_at.p;
+        cp.stop_items = (uint32_t *)stop_items.p;
+        cp.n_stop = (uint32_t *)counters.p + 6;
         return cp;
     }
     const uint32_t *sorted_vals() const { return (const uint32_t *)(sorted_in_b ? inst_b_v.p : inst_a_v.p); }
@@ -197,7 +200,8 @@ void release_state(lvigs_ctx *ctx, RenderState &s) {
     DevBuf *all[] = {&s.recs, &s.tiles, &s.zbits, &s.rects, &s.inst_a_t, &s.inst_a_v, &s.inst_b_t,
                      &s.inst_b_v, &s.ranges, &s.final_T, &s.n_contrib, &s.vs_dev, &s.counters,
                      &s.n_chunks, &s.chunk_base, &s.part_base, &s.pair_tile, &s.part,
-                     &s.pair_k, &s.pair_v, &s.pair_v2, &s.stop_at, &s.plan_aux, &s.pix_state};
+                     &s.pair_k, &s.pair_v, &s.pair_v2, &s.stop_at, &s.plan_aux, &s.stop_items,
+                     &s.pix_state};
     for (DevBuf *b : all) release(ctx, *b);
     s.valid = false;
     s.m_cap = 0;
@@ -323,6 +327,7 @@ lvigs_status ensure_plan(lvigs_ctx *ctx, RenderState &st) {
     LV_TRY(ensure(ctx, st.pair_v2, (size_t)pairs * 4));
     LV_TRY(ensure(ctx, st.stop_at, (size_t)st.vs.total_pixels * 4));
     LV_TRY(ensure(ctx, st.plan_aux, plan_aux_bytes(st.vs.total_tiles)));
+    LV_TRY(ensure(ctx, st.stop_items, (size_t)pairs * (st.vs.tile_w / 8) * (st.vs.tile_h / 8) * 4));
     LV_TRY(ensure(ctx, st.pix_state, (size_t)st.vs.total_pixels * pix_state_bytes()));
     LV_TRY(ensure(ctx, st.part, (size_t)slots * chunk_slot_bytes(st.vs.tile_w, st.vs.tile_h)));
     st.pair_cap = (uint32_t)pairs;

@@ -454,6 +454,23 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
             for (int q = 0; q < 6; ++q) f[j][q] = g[j][q];
         }
     }
+    // the block's stop chunks, each once, to the list of the exact walks
+    {
+        int v0 = stop[0], v1 = stop[1];
+        for (;;) {
+            const int cand = v0 >= 0 ? v0 : v1;
+            const uint32_t m = __ballot_sync(0xffffffffu, cand >= 0);
+            if (!m) break;
+            const int v = __shfl_sync(0xffffffffu, cand, __ffs(m) - 1);
+            if (lane == 0) {
+                const uint32_t pos = atomicAdd(cp.n_stop, 1u);
+                const uint32_t cap = cp.pair_cap * (uint32_t)Gm::NB;
+                if (pos < cap) cp.stop_items[pos] = (cp.chunk_base[gt] + (uint32_t)v) * Gm::NB + (uint32_t)blk;
+            }
+            if (v0 == v) v0 = -1;
+            if (v1 == v) v1 = -1;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         const int py = bp.py0 + j;
@@ -505,6 +522,8 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
 // Phase 2b: exact walk of each stop chunk from the true transmittance, one
 // (tile, chunk, block) item per warp, for the pixels that stop in that chunk.
 // Writes their final values and the chunk's contribution (backward state).
+// The items are the ones phase 2a listed (a block with a pixel stopping in
+// that chunk), so no warp visits a chunk only to find nothing to do.
 template <int TW, int TH, int BM>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
 combine_walk_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ ranges,
@@ -518,11 +537,12 @@ combine_walk_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
     __shared__ int sP[kWarpsPerCta][B];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
-    const uint32_t n_items = min(*cp.n_pairs, cp.pair_cap) * Gm::NB;
+    const uint32_t n_items = min(*cp.n_stop, cp.pair_cap * (uint32_t)Gm::NB);
     for (;;) {
-        const uint32_t item = take_item(queue, lane);
-        if (item >= n_items) break;
-        const uint32_t pair = cp.pair_order ? cp.pair_order[item / Gm::NB] : item / Gm::NB;
+        const uint32_t idx = take_item(queue, lane);
+        if (idx >= n_items) break;
+        const uint32_t item = cp.stop_items[idx];
+        const uint32_t pair = item / Gm::NB;
         const int blk = (int)(item % Gm::NB);
         if (pair >= cp.pair_cap) continue;
         const uint32_t gt = cp.pair_tile[pair];
@@ -1125,6 +1145,7 @@ void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, cons
                                                                       n_contrib, cp, queue);
     }
     if (part & 2) {
+        cudaMemsetAsync(cp.n_stop, 0, sizeof(uint32_t), s);
         combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, ranges, out, final_T, n_contrib, cp,
                                                                             ps, vs.total_tiles);
         cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);

@@ -218,6 +218,8 @@ struct ChunkPlan {
     uint32_t pair_cap, slot_cap;
     const uint32_t *pair_order; // [pair_cap] work order (chunk-major), or null
     uint32_t *stop_at;          // [total pixels] first chunk with a local stop (reset to ~0)
+    uint32_t *stop_items;       // [pair_cap * 8x8 blocks per tile] (pair, block) items with a stop
+    uint32_t *n_stop;           // device count of stop_items
 };
 // The plan from the tile ranges: n_chunks, chunk_base, part_base and
 // pair_tile of cp, counters[4] = pairs, counters[5] = slots, and the

@@ -30,6 +30,7 @@ constexpr int kRsThreads = kRsWarps * 32;
 constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems; // 2048
 constexpr int kRsMaxGrid = 1024; // row scan: one thread per block of the grid
+constexpr int kRsBlocksPerSm = 3; // downsweep occupancy (its launch bound)
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -311,7 +312,7 @@ radix_rowscan_kernel(uint32_t *counts, int G, uint32_t *totals) {
     if (t < G) counts[(size_t)d * G + t] = warp_sums[warp] + inc - x;
 }
 
-__global__ void __launch_bounds__(kRsThreads, 3)
+__global__ void __launch_bounds__(kRsThreads, kRsBlocksPerSm)
 radix_downsweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                        uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                        const uint32_t *n_dev, uint32_t n_host, int shift, int G, const uint32_t *counts,
@@ -523,9 +524,14 @@ __global__ void sum_i32_kernel(const int32_t *x, uint32_t n, unsigned long long 
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// One resident wave of the downsweep (kRsBlocksPerSm blocks per SM), each
+// block taking an equal run of whole tiles, so no block waits for a second
+// wave behind the others.
 int rs_grid(int64_t n_max) {
     int64_t g = (n_max + kRsTile - 1) / kRsTile;
+    const int64_t wave = (int64_t)device_sm_count() * kRsBlocksPerSm;
     if (g < 1) g = 1;
+    if (g > wave) g = wave;
     if (g > kRsMaxGrid) g = kRsMaxGrid;
     return (int)g;
 }
