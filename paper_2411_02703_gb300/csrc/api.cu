@@ -109,6 +109,10 @@ struct lvigs_ctx {
     int64_t render_m_cap = 0;
     bool step_pending = false;
     cudaStream_t cap_stream = nullptr;
+    // second stream of the batched step: the target pyramid, and the backward's
+    // start state and work order, run beside the main chain (graph branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev[4] = {};
     // one graph for steps with their own targets, one per staging slot
     cudaGraphExec_t graph_exec[1 + LVIGS_STAGE_SLOTS] = {};
     BatchKey graph_key[1 + LVIGS_STAGE_SLOTS];
@@ -245,6 +249,8 @@ struct Phase {
         if (st_ != LVIGS_OK) return st_;             \
     } while (0)
 
+// (Powers of two only: key preprocessing divides by the tile size as a
+// product with its exact reciprocal.)
 bool tile_supported(int w, int h) {
     return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 16);
 }
@@ -508,6 +514,9 @@ lvigs_status lvigs_create(lvigs_ctx **out, const lvigs_config *cfg) {
         e = cudaEventCreateWithFlags(&ctx->vs_event[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->step_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming);
     for (int k = 0; k < LVIGS_STAGE_SLOTS && e == cudaSuccess; ++k) {
         e = cudaEventCreateWithFlags(&ctx->stg_ready[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->stg_read[k], cudaEventDisableTiming);
@@ -556,6 +565,9 @@ void lvigs_destroy(lvigs_ctx *ctx) {
     for (cudaGraphExec_t ge : ctx->graph_exec)
         if (ge) cudaGraphExecDestroy(ge);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (cudaEvent_t ev : ctx->side_ev)
+        if (ev) cudaEventDestroy(ev);
     for (int k = 0; k < LVIGS_STAGE_SLOTS; ++k) {
         if (ctx->stg_ready[k]) cudaEventDestroy(ctx->stg_ready[k]);
         if (ctx->stg_read[k]) cudaEventDestroy(ctx->stg_read[k]);
@@ -635,7 +647,8 @@ lvigs_status render_view(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_c
         Phase ph(ctx, part == 1 ? LVIGS_PHASE_COMPOSITE_FWD : LVIGS_PHASE_COMBINE, s);
         launch_composite_fwd(st.vs, (const ViewSet *)st.vs_dev.p, (const uint2 *)st.ranges.p, st.sorted_vals(),
                              (const GRec *)st.recs.p, im, (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(),
-                             (uint32_t *)st.counters.p + 3, st.pix_state.p, s, ctx->bm, part);
+                             (uint32_t *)st.counters.p + 3, st.pix_state.p, s, ctx->bm,
+                             part == 1 ? kFwdWalk : kFwdCombine | kFwdBackwardState);
     }
     LV_CUDA(cudaGetLastError());
     st.valid = true;
@@ -903,10 +916,20 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         gt_l[v] = gsrc;
         li_l[v] = lsrc;
     }
-    {
-        Phase ph(ctx, LVIGS_PHASE_PYRAMID, s);
-        for (int l = 1; l <= LVIGS_MAX_LEVEL; ++l) launch_pyramid_views(pv[l], l, s);
+    // The side stream takes the pyramid (needed by the loss only) and later the
+    // backward's start state and work order (needed by the backward only).
+    // With the phase profiler on, everything runs in order on `s`.
+    const bool par = !ctx->prof;
+    cudaStream_t ss = par ? ctx->side : s;
+    if (par) {
+        LV_CUDA(cudaEventRecord(ctx->side_ev[0], s));
+        LV_CUDA(cudaStreamWaitEvent(ss, ctx->side_ev[0], 0));
     }
+    {
+        Phase ph(ctx, LVIGS_PHASE_PYRAMID, ss);
+        for (int l = 1; l <= LVIGS_MAX_LEVEL; ++l) launch_pyramid_views(pv[l], l, ss);
+    }
+    if (par) LV_CUDA(cudaEventRecord(ctx->side_ev[1], ss));
     // 2. a1-a4 over all views at once; preprocessing also clears the gradient
     // records of the pairs the backward will read (forward and backward of one
     // call, so nothing else writes them in between)
@@ -958,9 +981,22 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     const ViewSet *vsd = (const ViewSet *)st.vs_dev.p;
     for (int part = 1; part <= 2; ++part) {
         Phase ph(ctx, part == 1 ? LVIGS_PHASE_COMPOSITE_FWD : LVIGS_PHASE_COMBINE, s);
+        const int what = part == 1 ? kFwdWalk : (par ? kFwdCombine : kFwdCombine | kFwdBackwardState);
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
                              (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
-                             st.pix_state.p, s, ctx->bm, part);
+                             st.pix_state.p, s, ctx->bm, what);
+    }
+    // the images are final: the backward's start state and work order beside the loss
+    ChunkPlan bp{};
+    if (par) {
+        LV_CUDA(cudaEventRecord(ctx->side_ev[2], s));
+        LV_CUDA(cudaStreamWaitEvent(ss, ctx->side_ev[2], 0));
+        launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
+                             (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
+                             st.pix_state.p, ss, ctx->bm, kFwdBackwardState);
+        bp = backward_plan(ctx, st, ss);
+        LV_CUDA(cudaEventRecord(ctx->side_ev[3], ss));
+        LV_CUDA(cudaStreamWaitEvent(s, ctx->side_ev[1], 0)); // the pyramid, for the loss
     }
     // 4. a8: loss and its image gradients for every view
     {
@@ -968,9 +1004,10 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         launch_loss(lv, ctx->loss_tmp.p, s);
     }
     // 5. a6 + a7
+    if (par) LV_CUDA(cudaStreamWaitEvent(s, ctx->side_ev[3], 0));
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
-        const ChunkPlan bp = backward_plan(ctx, st, s);
+        if (!par) bp = backward_plan(ctx, st, s);
         launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
                              (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, bp,
                              (uint32_t *)st.counters.p + 3, s, ctx->bm);

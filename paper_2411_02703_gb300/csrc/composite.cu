@@ -1138,13 +1138,13 @@ void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, cons
     const uint64_t max_items = (uint64_t)cp.pair_cap * Gm::NB;
     const uint64_t tw = (uint64_t)vs.total_tiles * Gm::NB;
     const unsigned grid_tiles = (unsigned)((tw + kWarpsPerCta - 1) / kWarpsPerCta);
-    if (part & 1) {
+    if (part & kFwdWalk) {
         cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
         composite_fwd_kernel<TW, TH, BM><<<persistent_grid(composite_fwd_kernel<TW, TH, BM>, max_items),
                                            kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
                                                                       n_contrib, cp, queue);
     }
-    if (part & 2) {
+    if (part & kFwdCombine) {
         cudaMemsetAsync(cp.n_stop, 0, sizeof(uint32_t), s);
         combine_scan_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, ranges, out, final_T, n_contrib, cp,
                                                                             ps, vs.total_tiles);
@@ -1152,8 +1152,9 @@ void fwd_launch(const ViewSet &vs, const ViewSet *vsd, const uint2 *ranges, cons
         combine_walk_kernel<TW, TH, BM><<<persistent_grid(combine_walk_kernel<TW, TH, BM>, max_items),
                                           kWarpsPerCta * 32, 0, s>>>(vsd, ranges, inst_vals, recs, out, final_T,
                                                                      n_contrib, cp, ps, queue);
-        combine_state_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, cp, ps, vs.total_tiles);
     }
+    if (part & kFwdBackwardState)
+        combine_state_kernel<TW, TH><<<grid_tiles, kWarpsPerCta * 32, 0, s>>>(vsd, cp, ps, vs.total_tiles);
 }
 
 template <int TW, int TH, int BM>

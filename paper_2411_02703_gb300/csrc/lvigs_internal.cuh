@@ -241,11 +241,15 @@ void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan
 // each stages 32 * bm Gaussians per round (bm = 1 or 2).  `queue` is one device
 // word (the work counter; reset by the launcher).
 // pix_state: pix_state_bytes() per pixel of the view set (forward scratch).
+// `part` of launch_composite_fwd: any of the bits below, in this order: the
+// chunk walks (phase 1), the combine and exact stop walks (the images are
+// final after it), the state each backward chunk walk starts from.
+constexpr int kFwdWalk = 1, kFwdCombine = 2, kFwdBackwardState = 4;
 size_t pix_state_bytes();
 void launch_composite_fwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewImages &out, float *final_T, int32_t *n_contrib,
                           const ChunkPlan &cp, uint32_t *queue, void *pix_state, cudaStream_t s, int bm,
-                          int part); // part: 1 per-chunk compositing, 2 combine of long lists, 3 both
+                          int part);
 void launch_composite_bwd(const ViewSet &vs, const ViewSet *vs_dev, const uint2 *ranges, const uint32_t *inst_vals,
                           const GRec *recs, const ViewGrads &g, const float *final_T, const int32_t *n_contrib,
                           GGrad *g2d, const ChunkPlan &cp, uint32_t *queue, cudaStream_t s, int bm);

@@ -350,6 +350,9 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
         opacity = 1.f / (1.f + expf(-P.opacity_logits[g]));
     }
     const float tw = (float)vsp->tile_w, th = (float)vsp->tile_h;
+    // tile sizes are powers of two (8, 16, 32): the reciprocals are exact and
+    // a product with one is the correctly rounded quotient, bit for bit
+    const float itw = 1.f / tw, ith = 1.f / th;
     const int n_views = vsp->n_views;
 
     // depth key of every pair; pairs in front of the near plane go on to the rest
@@ -445,10 +448,10 @@ preprocess_fwd_kernel(GaussParams P, const ViewSet *__restrict__ vsp, GRec *__re
         uint2 rect = make_uint2(0, 0);
         if (vis) {
             const float fr = (float)rad;
-            const int x0 = (int)tile_coord(RN_DIV(RN_SUB(u, fr), tw), V.tiles_x);
-            const int x1 = (int)tile_coord(RN_DIV(RN_ADD(RN_ADD(u, fr), tw - 1.f), tw), V.tiles_x);
-            const int y0 = (int)tile_coord(RN_DIV(RN_SUB(v, fr), th), V.tiles_y);
-            const int y1 = (int)tile_coord(RN_DIV(RN_ADD(RN_ADD(v, fr), th - 1.f), th), V.tiles_y);
+            const int x0 = (int)tile_coord(RN_MUL(RN_SUB(u, fr), itw), V.tiles_x);
+            const int x1 = (int)tile_coord(RN_MUL(RN_ADD(RN_ADD(u, fr), tw - 1.f), itw), V.tiles_x);
+            const int y0 = (int)tile_coord(RN_MUL(RN_SUB(v, fr), ith), V.tiles_y);
+            const int y1 = (int)tile_coord(RN_MUL(RN_ADD(RN_ADD(v, fr), th - 1.f), ith), V.tiles_y);
             ntiles = (uint32_t)((x1 - x0) * (y1 - y0));
             rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
         }
