@@ -346,20 +346,31 @@ __global__ void prune_flags_kernel(const float *__restrict__ logits, int64_t n, 
 
 // Pruning, first pass: the kept rows of every buffer (blockIdx.y picks the
 // buffer) to consecutive rows of its scratch segment.  Rows are taken in
-// chunks of kPruneRows so the row of an element comes from a 32-bit divide.
-// Nothing is done when every row is kept (offs[n] == n).
+// chunks of kPruneRows whose keep flags and destinations are staged in shared
+// memory; an element's row comes from a product with 1/w, corrected to the
+// exact quotient.  Nothing is done when every row is kept (offs[n] == n).
 constexpr int kPruneRows = 256;
 __global__ void __launch_bounds__(256) prune_compact_kernel(PruneArgs A) {
+    __shared__ uint32_t s_keep[kPruneRows], s_offs[kPruneRows];
     const int64_t n = A.n;
     if ((int64_t)A.offs[n] == n) return;
     const PruneSeg S = A.seg[blockIdx.y];
     const uint32_t w = (uint32_t)S.w;
+    const float inv_w = 1.f / (float)w;
     for (int64_t r0 = (int64_t)blockIdx.x * kPruneRows; r0 < n; r0 += (int64_t)gridDim.x * kPruneRows) {
         const uint32_t rows = (uint32_t)min((int64_t)kPruneRows, n - r0);
+        __syncthreads(); // the previous chunk's flags are no longer read
+        for (uint32_t i = threadIdx.x; i < rows; i += blockDim.x) {
+            s_keep[i] = A.keep[r0 + i];
+            s_offs[i] = A.offs[r0 + i];
+        }
+        __syncthreads();
         const float *src = S.buf + r0 * w;
         for (uint32_t e = threadIdx.x; e < rows * w; e += blockDim.x) {
-            const uint32_t r = e / w;
-            if (A.keep[r0 + r]) S.tmp[(int64_t)A.offs[r0 + r] * w + (e - r * w)] = src[e];
+            uint32_t r = __float2uint_rz(((float)e + 0.5f) * inv_w);
+            if (r * w > e) --r;
+            else if ((r + 1) * w <= e) ++r;
+            if (s_keep[r]) S.tmp[(int64_t)s_offs[r] * w + (e - r * w)] = src[e];
         }
     }
 }
@@ -452,12 +463,13 @@ void launch_prune_flags(const float *logits, int64_t n, float thr, uint32_t *kee
 
 void launch_prune_compact(const PruneArgs &A, cudaStream_t s) {
     if (A.n <= 0 || A.nseg <= 0) return;
+    // a full grid for every buffer: the SH buffers hold most of the bytes and
+    // need many loads in flight; the blocks of the small ones finish early
     const int sms = device_sm_count();
     const int64_t chunks = (A.n + kPruneRows - 1) / kPruneRows;
-    const int gx1 = (int)std::min<int64_t>(chunks, std::max<int64_t>(1, (int64_t)sms * 8 / A.nseg));
+    const int gx1 = (int)std::min<int64_t>(chunks, (int64_t)sms * 8);
     prune_compact_kernel<<<dim3(gx1, A.nseg), 256, 0, s>>>(A);
-    const int gx2 = std::max(1, sms * 8 / A.nseg);
-    prune_copy_back_kernel<<<dim3(gx2, A.nseg), 256, 0, s>>>(A);
+    prune_copy_back_kernel<<<dim3(sms * 8, A.nseg), 256, 0, s>>>(A);
 }
 
 } // namespace lvigs

@@ -246,7 +246,9 @@ __device__ __forceinline__ void stage_sh_rows_t(const float *__restrict__ src, i
                                                 float *__restrict__ dst) {
     if (ROW) row = ROW;
     const int n = nrows * row;
-    if ((((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
+    // (only the compile-time row takes the unrolled path: one copy of it keeps
+    // the kernels' code small)
+    if (ROW && (((uintptr_t)src) & 15u) == 0 && (n & 3) == 0) {
         constexpr int kMaxIt = 32 * kShRow / 4 / 32;
         float4 v[kMaxIt];
 #pragma unroll
