@@ -1050,21 +1050,36 @@ plan_place_kernel(uint32_t n_tiles, const uint32_t *__restrict__ n_chunks, uint3
     const uint32_t c = t < n_tiles ? n_chunks[t] : 0u;
     uint32_t cb = c, pb = c > 1 ? c : 0u, ta, tb;
     block_scan2(cb, pb, ta, tb);
-    if (t >= n_tiles) return;
-    cb += aux[kAuxBlocks + 2 * blockIdx.x];
-    pb += aux[kAuxBlocks + 2 * blockIdx.x + 1];
-    chunk_base[t] = cb;
-    part_base[t] = pb;
-    if (c > 1 && pb + c > slot_cap) atomicOr(status, kStatusCapacity);
-    if (cb + c > pair_cap) {
-        atomicOr(status, kStatusCapacity);
-        return;
+    bool ok = t < n_tiles;
+    if (ok) {
+        cb += aux[kAuxBlocks + 2 * blockIdx.x];
+        pb += aux[kAuxBlocks + 2 * blockIdx.x + 1];
+        chunk_base[t] = cb;
+        part_base[t] = pb;
+        if (c > 1 && pb + c > slot_cap) atomicOr(status, kStatusCapacity);
+        if (cb + c > pair_cap) {
+            atomicOr(status, kStatusCapacity);
+            ok = false;
+        }
     }
-    for (uint32_t k = 0; k < c; ++k) pair_tile[cb + k] = t;
-    order[t] = cb;
-    for (uint32_t k = 1; k < c; ++k) {
-        const uint32_t pos = atomicAdd(aux + min(k, kOrderBuckets - 1), 1u);
-        if (pos < pair_cap) order[pos] = cb + k;
+    if (ok) {
+        for (uint32_t k = 0; k < c; ++k) pair_tile[cb + k] = t;
+        order[t] = cb;
+    }
+    // later chunks: one atomic per warp and chunk index (the lanes that have
+    // a k-th chunk take consecutive positions)
+    const uint32_t kc = ok ? c : 0u;
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, kc);
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t k = 1; k < kmax; ++k) {
+        const uint32_t m = __ballot_sync(0xffffffffu, k < kc);
+        uint32_t base = 0;
+        if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(aux + min(k, kOrderBuckets - 1), (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (k < kc) {
+            const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < pair_cap) order[pos] = cb + k;
+        }
     }
 }
 
@@ -1073,9 +1088,22 @@ plan_place_kernel(uint32_t n_tiles, const uint32_t *__restrict__ n_chunks, uint3
 __global__ void bucket_place_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_dev, uint32_t cap,
                                     uint32_t *__restrict__ aux, uint32_t *__restrict__ order) {
     const uint32_t n = min(*n_dev, cap);
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const uint32_t pos = atomicAdd(aux + (keys[p] & (kOrderBuckets - 1)), 1u);
-        if (pos < n) order[pos] = p;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // whole warps iterate (the ones past n idle), so the lanes with one key
+    // take consecutive positions with one atomic
+    for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < n; p0 += stride) {
+        const uint32_t p = p0 + lane;
+        const uint32_t key = p < n ? (keys[p] & (kOrderBuckets - 1)) : kOrderBuckets;
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const int lead = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (key < kOrderBuckets && (int)lane == lead) base = atomicAdd(aux + key, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, lead);
+        if (key < kOrderBuckets) {
+            const uint32_t pos = base + __popc(peers & ((1u << lane) - 1u));
+            if (pos < n) order[pos] = p;
+        }
     }
 }
 
@@ -1089,6 +1117,9 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
                                      const int32_t *__restrict__ n_contrib, uint32_t *__restrict__ keys,
                                      uint32_t *__restrict__ aux) {
     using Gm = Geometry<TW, TH>;
+    __shared__ uint32_t hist[kOrderBuckets];
+    for (uint32_t i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
     const uint32_t n = min(*cp.n_pairs, cp.pair_cap);
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -1112,9 +1143,12 @@ __global__ void bwd_pair_keys_kernel(const ViewSet *__restrict__ vsp, ChunkPlan 
         }
         if (lane == 0) {
             keys[p] = key;
-            atomicAdd(aux + key, 1u);
+            atomicAdd(&hist[key], 1u);
         }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kOrderBuckets; i += blockDim.x)
+        if (hist[i]) atomicAdd(aux + i, hist[i]);
     if (last_block(aux + kAuxTicket)) bucket_starts(aux);
 }
 
