@@ -329,7 +329,7 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
         const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
         const uint2 rg = ranges[gt];
         const uint32_t lo = rg.x + k * (uint32_t)cp.L;
-        const uint32_t hi = min(rg.y, lo + (uint32_t)cp.L);
+        const uint32_t hi = nch <= 1 ? rg.y : min(rg.y, lo + (uint32_t)cp.L);
         float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
         int last[PPT];
         bool done[PPT], stopped[PPT];
@@ -826,7 +826,7 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
         }
         const int warp_last = __reduce_max_sync(0xffffffffu, max(last[0], last[1]));
         const uint32_t lo_chunk = rg.x + k * (uint32_t)cp.L;
-        const uint32_t end = min(min(rg.y, lo_chunk + (uint32_t)cp.L), rg.x + (uint32_t)warp_last);
+        const uint32_t end = min(nch <= 1 ? rg.y : min(rg.y, lo_chunk + (uint32_t)cp.L), rg.x + (uint32_t)warp_last);
 
         for (uint32_t hi = end; hi > lo_chunk;) {
             const uint32_t lo = hi - lo_chunk > (uint32_t)B ? hi - B : lo_chunk;
@@ -893,7 +893,8 @@ composite_bwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
 }
 
 // List-parallel plan: per tile the number of chunks (an empty tile still has
-// one), its first pair and, for a multi-chunk tile, its first slot (exclusive
+// one; a list of up to 1.5 L entries stays one chunk: the combine of two
+// chunks costs more than the longer item), its first pair and, for a multi-chunk tile, its first slot (exclusive
 // scans over the tiles), the tile of every pair, and the forward work order:
 // pairs by chunk index, all first chunks (in tile order), then all second
 // chunks, ... (chunks from the 255th on share the last bucket).  Within a
@@ -999,7 +1000,7 @@ plan_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L
     if (t < n_tiles) {
         const uint2 r = ranges[t];
         const uint32_t len = r.y - r.x;
-        c = len > L ? (len + L - 1) / L : 1u;
+        c = len > L + L / 2 ? (len + L - 1) / L : 1u; // up to 1.5 chunks stay one item
         n_chunks[t] = c;
         // bucket k > 0 counts the tiles with more than k chunks
         const uint32_t kc = min(c, kOrderBuckets - 1);
