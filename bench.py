@@ -161,10 +161,10 @@ PHASE_SOURCE = {"composite_fwd": "composite.cu", "composite_bwd": "composite.cu"
                 "preprocess": "preprocess.cu", "preprocess_bwd": "preprocess.cu", "loss": "loss.cu", "adam": "map.cu"}
 
 
-def recorded_traffic(phase):
+def recorded_traffic(phase, workload):
     """DRAM bytes per launch of the phase's kernel from profiles/dram_traffic.md
     (lines `phase kernel source_sha256 bytes_per_launch workload`), or None
-    when no capture matches the current source."""
+    when no capture matches the current source and the workload."""
     import hashlib
 
     src = PHASE_SOURCE.get(phase)
@@ -177,7 +177,7 @@ def recorded_traffic(phase):
             for line in f:
                 parts = line.strip().strip("|").split("|")
                 parts = [x.strip() for x in parts]
-                if len(parts) >= 5 and parts[0] == phase and parts[2] == sha:
+                if len(parts) >= 5 and parts[0] == phase and parts[2] == sha and parts[4] == workload:
                     return float(parts[3])
     except OSError:
         return None
@@ -411,7 +411,7 @@ def run_ours(args):
     d2h = V * 4 * 8
 
     map_ops = None if args.skip_map else time_map_ops(P, S, lv, params, grads, cams[0], stream, peaks()[0],
-                                                       peaks()[2])
+                                                       peaks()[2], args.workload)
 
     n_vis, M, nc_sum, P_px = stats
     # instances the compositing kernels gather: bounded by M; use M (upper bound)
@@ -428,14 +428,14 @@ def run_ours(args):
     if dominant in flops:
         roof = {"bound": "alu", "kernel": dominant, "achieved": flops[dominant] / t_dom / 1e12,
                 "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": recorded_traffic(dominant),
+                "frac": flops[dominant] / t_dom / 1e12 / alu_peak, "traffic": recorded_traffic(dominant, args.workload),
                 "peak_source": f"{n_sm} SM x 128 FP32 lanes x 2 x sm_max_mhz",
                 "flop_per_pair": FLOP_PER_PAIR[dominant],
                 "hbm_achieved_gbs": ab[dominant] / t_dom / 1e9}
     else:
         ach = ab[dominant] / t_dom / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": recorded_traffic(dominant), "peak_source": peak_kind}
+                "frac": ach / hbm_peak, "traffic": recorded_traffic(dominant, args.workload), "peak_source": peak_kind}
     roof["step"], roof["phases"] = roofline_table(phase_ms, ab, flops, ms_batched, hbm_peak, alu_peak)
     roof["step"]["peak_source"] = peak_kind
 
@@ -643,7 +643,7 @@ def run_mapping(args):
         print(json.dumps(out))
 
 
-def time_map_ops(P, S, lv, params, grads, cam, stream, hbm_peak, peak_kind):
+def time_map_ops(P, S, lv, params, grads, cam, stream, hbm_peak, peak_kind, workload):
     """Map maintenance on the bench's map: the Adam step over every parameter
     (HBM-bound: read parameter, gradient and both moments, write parameter and
     moments, 28 B per float), expansion by one 50,000-point sweep (with and
@@ -705,7 +705,7 @@ def time_map_ops(P, S, lv, params, grads, cam, stream, hbm_peak, peak_kind):
         ts.append((time.perf_counter() - t0) * 1e3)
     ms_prune = float(np.median(ts[1:]))
     del saved
-    return {"adam": {"ms": round(ms_adam, 4), "bytes": adam_bytes, "traffic": recorded_traffic("adam"),
+    return {"adam": {"ms": round(ms_adam, 4), "bytes": adam_bytes, "traffic": recorded_traffic("adam", workload),
                      "achieved_gbs": round(adam_bytes / ms_adam / 1e6, 1),
                      "frac": round(adam_bytes / ms_adam / 1e6 / hbm_peak, 3), "peak": hbm_peak,
                      "peak_source": peak_kind, "floats": N * (11 + 3 * K)},
