@@ -438,9 +438,9 @@ lvigs_status build_lists(lvigs_ctx *ctx, RenderState &st, cudaStream_t s, bool e
     return LVIGS_OK;
 }
 
-// The backward's work order: the plan's pairs sorted by decreasing expected
-// walk (written over the forward's order, which the forward no longer needs).
-ChunkPlan backward_plan(lvigs_ctx *ctx, RenderState &st, cudaStream_t s) {
+// The backward's work order: the plan's pairs by decreasing expected walk (in
+// its own buffer; the forward's order stays as it was).
+ChunkPlan backward_plan(RenderState &st, cudaStream_t s) {
     ChunkPlan cp = st.plan();
     uint32_t *cnt = (uint32_t *)st.counters.p;
     launch_bwd_pair_keys(st.vs, (const ViewSet *)st.vs_dev.p, cp, (const int32_t *)st.n_contrib.p,
@@ -690,7 +690,7 @@ lvigs_status lvigs_backward(lvigs_ctx *ctx, int view_slot, const float *dL_drgb,
     vg.d_alpha[0] = dL_dalpha;
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
-        const ChunkPlan bp = backward_plan(ctx, *st, s);
+        const ChunkPlan bp = backward_plan(*st, s);
         launch_composite_bwd(st->vs, (const ViewSet *)st->vs_dev.p, (const uint2 *)st->ranges.p, st->sorted_vals(),
                              (const GRec *)st->recs.p, vg, (const float *)st->final_T.p,
                              (const int32_t *)st->n_contrib.p, (GGrad *)ctx->g2d.p, bp,
@@ -994,7 +994,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
         launch_composite_fwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, im,
                              (float *)st.final_T.p, (int32_t *)st.n_contrib.p, st.plan(), (uint32_t *)st.counters.p + 3,
                              st.pix_state.p, ss, ctx->bm, kFwdBackwardState);
-        bp = backward_plan(ctx, st, ss);
+        bp = backward_plan(st, ss);
         LV_CUDA(cudaEventRecord(ctx->side_ev[3], ss));
         LV_CUDA(cudaStreamWaitEvent(s, ctx->side_ev[1], 0)); // the pyramid, for the loss
     }
@@ -1007,7 +1007,7 @@ lvigs_status batched_body(lvigs_ctx *ctx, const lvigs_gaussians *g, const lvigs_
     if (par) LV_CUDA(cudaStreamWaitEvent(s, ctx->side_ev[3], 0));
     {
         Phase ph(ctx, LVIGS_PHASE_COMPOSITE_BWD, s);
-        if (!par) bp = backward_plan(ctx, st, s);
+        if (!par) bp = backward_plan(st, s);
         launch_composite_bwd(st.vs, vsd, (const uint2 *)st.ranges.p, st.sorted_vals(), (const GRec *)st.recs.p, vg,
                              (const float *)st.final_T.p, (const int32_t *)st.n_contrib.p, (GGrad *)ctx->g2d.p, bp,
                              (uint32_t *)st.counters.p + 3, s, ctx->bm);

@@ -1262,7 +1262,7 @@ void launch_bwd_pair_keys(const ViewSet &vs, const ViewSet *vsd, const ChunkPlan
     if (cp.pair_cap == 0) return;
     cudaMemsetAsync(aux, 0, sizeof(uint32_t) * kAuxBlocks, s);
     uint64_t blocks = ((uint64_t)cp.pair_cap * 32 + 255) / 256;
-    if (blocks > device_sm_count() * 16) blocks = device_sm_count() * 16;
+    if (blocks > (uint64_t)device_sm_count() * 16) blocks = (uint64_t)device_sm_count() * 16;
     if (vs.tile_w == 16 && vs.tile_h == 16)
         bwd_pair_keys_kernel<16, 16><<<(unsigned)blocks, 256, 0, s>>>(vsd, cp, n_contrib, keys, aux);
     else if (vs.tile_w == 8 && vs.tile_h == 8)

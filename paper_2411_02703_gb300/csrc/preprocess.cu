@@ -563,7 +563,8 @@ __device__ __forceinline__ void write_sh_grad_rows(float *__restrict__ dst, int 
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int rw = (e + c) / ROW, col = (e + c) - rw * ROW;
+                constexpr int R = ROW ? ROW : 1; // (this branch is taken with ROW only)
+                const int rw = (e + c) / R, col = (e + c) - rw * R;
                 const bool live = col < live_cols && col < kShRow;
                 v[c] = live ? (accumulate ? o[c] + acc[col * ld + wbase + rw] : acc[col * ld + wbase + rw])
                             : (accumulate ? o[c] : 0.f);
