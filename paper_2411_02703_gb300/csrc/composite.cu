@@ -505,12 +505,21 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
                 m = mm + 1;
             }
             if (m > 0) {
-                st.Tc = __fmul_rn(T[j], Tm[m - 1]);
+                // (selected with constant indices, so the arrays stay in registers)
+                float tsel = 0.f;
+                int lsel = 0;
+#pragma unroll
+                for (int mm = 0; mm < kSub - 1; ++mm)
+                    if (mm == m - 1) {
+                        tsel = Tm[mm];
+                        lsel = lm[mm];
+                    }
+                st.Tc = __fmul_rn(T[j], tsel);
                 st.Cc0 = fmaf(T[j], slot_group(cp, sl, m - 1, 0, TPX)[lp], C0[j]);
                 st.Cc1 = fmaf(T[j], slot_group(cp, sl, m - 1, 1, TPX)[lp], C1[j]);
                 st.Cc2 = fmaf(T[j], slot_group(cp, sl, m - 1, 2, TPX)[lp], C2[j]);
                 st.Dc = fmaf(T[j], slot_group(cp, sl, m - 1, 3, TPX)[lp], D[j]);
-                if (lm[m - 1]) st.lastc = lm[m - 1];
+                if (lsel) st.lastc = lsel;
             }
             st.sub = m;
         }
