@@ -55,6 +55,10 @@ struct RenderState {
         cp.part_base = (const uint32_t *)part_base.p;
         cp.pair_tile = (const uint32_t *)pair_tile.p;
         cp.n_pairs = (const uint32_t *)counters.p + 4;
+        cp.n_fwd = (const uint32_t *)counters.p + 7;
+        cp.n_inst = (const uint32_t *)counters.p + 2;
+        cp.nb = (vs.tile_w / 8) * (vs.tile_h / 8);
+        cp.warps = (uint32_t)device_sm_count() * 24; // six 4-warp CTAs per SM
         cp.part = (float *)part.p;
         cp.pair_cap = pair_cap;
         cp.slot_cap = slot_cap;

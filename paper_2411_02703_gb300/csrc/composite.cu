@@ -56,6 +56,20 @@ constexpr int PPT = 2; // pixels per lane (rows 2r, 2r+1 of the block)
 constexpr int kWarpsPerCta = 4;
 constexpr int kFields = 6; // per (pixel, chunk) slot and checkpoint
 constexpr int kSub = 8;    // checkpoint groups per chunk: after each eighth (the last is the chunk's end)
+// Lists of 2 .. w chunks are walked whole by one forward warp (the true
+// transmittance throughout, so its stops are exact and no combine is needed),
+// which writes each chunk's slot in the form the backward starts from; longer
+// lists are walked chunk-parallel and combined.  Such an item must not
+// outlast the rest of the work: w is the chunk count of about 1.25 times the
+// average walk per resident warp (instances x blocks per tile / warps), at
+// most kWholeMax, computed alike by every kernel from the instance count.
+constexpr uint32_t kWholeMax = 8;
+__device__ __forceinline__ uint32_t whole_max(const ChunkPlan &cp) {
+    const uint64_t per_warp = (uint64_t)(*cp.n_inst) * (uint64_t)cp.nb / (uint64_t)(cp.warps ? cp.warps : 1u);
+    const uint64_t w = per_warp * 5 / (4 * (uint64_t)cp.L);
+    return w < kWholeMax ? (uint32_t)w : kWholeMax;
+}
+__device__ __forceinline__ bool whole_list(uint32_t nch, uint32_t wmax) { return nch >= 2 && nch <= wmax; }
 
 // Can record (a, b, c) reach alpha >= 1/255 anywhere in the block
 // [x0, x0+7] x [y0, y0+7]?  First the conservative box of that region
@@ -312,7 +326,8 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
     __shared__ int sP[kWarpsPerCta][B];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Smem sm{sA[w], sB[w], sC[w], sP[w], nullptr};
-    const uint32_t n_items = min(*cp.n_pairs, cp.pair_cap) * Gm::NB;
+    const uint32_t n_items = min(*cp.n_fwd, cp.pair_cap) * Gm::NB;
+    const uint32_t wmax = whole_max(cp);
     for (;;) {
         const uint32_t item = take_item(queue, lane);
         if (item >= n_items) break;
@@ -324,13 +339,13 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
         const uint32_t nch = cp.n_chunks[gt];
         const uint32_t k = pair - cp.chunk_base[gt];
         if (k >= nch) continue;
+        const bool whole = whole_list(nch, wmax);
+        if (whole && (k != 0 || cp.part_base[gt] + nch > cp.slot_cap)) continue; // (overflow latched)
         const int vi = view_of_tile(*vsp, gt);
         const ViewDesc &V = vsp->v[vi];
         const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
         const uint2 rg = ranges[gt];
-        const uint32_t lo = rg.x + k * (uint32_t)cp.L;
-        const uint32_t hi = nch <= 1 ? rg.y : min(rg.y, lo + (uint32_t)cp.L);
-        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT];
         int last[PPT];
         bool done[PPT], stopped[PPT];
 #pragma unroll
@@ -341,16 +356,45 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
             done[j] = !(bp.px < V.W && bp.py0 + j < V.H);
             stopped[j] = false;
             // a pixel known to stop in an earlier chunk needs nothing from this one
-            if (!done[j] && nch > 1) {
+            if (!done[j] && nch > 1 && !whole) {
                 const size_t gp = V.pix_base + (size_t)(bp.py0 + j) * V.W + bp.px;
                 if (__ldcg(cp.stop_at + gp) < k) done[j] = true;
             }
         }
-        Checkpoints ck{nullptr, cp.L / kSub, Gm::TPX, bp.lp0, TW};
-        if (nch > 1 && cp.part_base[gt] + k < cp.slot_cap) ck.g0 = slot_group(cp, cp.part_base[gt] + k, 0, 0, Gm::TPX);
-        fwd_walk<BM, true, false>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane, T, C0,
-                                  C1, C2, D, last, done, stopped, ck, nullptr);
-        if (nch > 1) {
+        // one chunk, or every chunk of a list walked whole (from the true
+        // state: the transmittance runs on, the sums restart per chunk)
+        const uint32_t k_end = whole ? nch : k + 1;
+        for (uint32_t kk = k; kk < k_end; ++kk) {
+            const uint32_t lo = rg.x + kk * (uint32_t)cp.L;
+            const uint32_t hi = (nch <= 1 || kk + 1 == nch) ? rg.y : min(rg.y, lo + (uint32_t)cp.L);
+            Checkpoints ck{nullptr, cp.L / kSub, Gm::TPX, bp.lp0, TW};
+            if (nch > 1 && !whole && cp.part_base[gt] + k < cp.slot_cap)
+                ck.g0 = slot_group(cp, cp.part_base[gt] + k, 0, 0, Gm::TPX);
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                Tin[j] = T[j];
+                if (whole) C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+            }
+            fwd_walk<BM, true, false>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane,
+                                      T, C0, C1, C2, D, last, done, stopped, ck, nullptr);
+            if (whole) {
+                // the chunk's contribution, the transmittance it removes and the
+                // one at its end: the state its backward walk starts from, once
+                // the sums of what lies behind are added in (combine_state)
+                const uint32_t slot = cp.part_base[gt] + kk;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const int lp = bp.lp0 + j * TW;
+                    slot_field(cp, slot, 0, Gm::TPX)[lp] = C0[j];
+                    slot_field(cp, slot, 1, Gm::TPX)[lp] = C1[j];
+                    slot_field(cp, slot, 2, Gm::TPX)[lp] = C2[j];
+                    slot_field(cp, slot, 3, Gm::TPX)[lp] = D[j];
+                    slot_field(cp, slot, 4, Gm::TPX)[lp] = Tin[j] - T[j];
+                    slot_field(cp, slot, 5, Gm::TPX)[lp] = T[j];
+                }
+            }
+        }
+        if (nch > 1 && !whole) {
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
                 if (stopped[j]) atomicMin(cp.stop_at + V.pix_base + (size_t)(bp.py0 + j) * V.W + bp.px, k);
@@ -360,6 +404,22 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
             for (int j = 0; j < PPT; ++j)
                 write_final(V, out, vi, final_T, n_contrib, bp.px, bp.py0 + j, T[j], C0[j], C1[j], C2[j], D[j],
                             last[j]);
+        } else if (whole) {
+            // colour and depth: the chunks' contributions in order (this
+            // thread's own stores, read back)
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int lp = bp.lp0 + j * TW;
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f, SD = 0.f;
+                for (uint32_t kk = 0; kk < nch; ++kk) {
+                    const uint32_t slot = cp.part_base[gt] + kk;
+                    S0 += slot_field(cp, slot, 0, Gm::TPX)[lp];
+                    S1 += slot_field(cp, slot, 1, Gm::TPX)[lp];
+                    S2 += slot_field(cp, slot, 2, Gm::TPX)[lp];
+                    SD += slot_field(cp, slot, 3, Gm::TPX)[lp];
+                }
+                write_final(V, out, vi, final_T, n_contrib, bp.px, bp.py0 + j, T[j], S0, S1, S2, SD, last[j]);
+            }
         } else {
             const uint32_t slot = cp.part_base[gt] + k;
             if (slot >= cp.slot_cap) continue; // capacity overflow is latched by the planner
@@ -405,7 +465,7 @@ combine_scan_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ r
     const uint32_t gt = item / Gm::NB;
     const int blk = (int)(item % Gm::NB);
     const uint32_t nch = cp.n_chunks[gt];
-    if (nch <= 1) return;
+    if (nch <= 1 || whole_list(nch, whole_max(cp))) return; // final after phase 1
     const uint32_t s0 = cp.part_base[gt];
     if (s0 + nch > cp.slot_cap) return; // capacity overflow is latched by the planner
     const int vi = view_of_tile(*vsp, gt);
@@ -640,6 +700,8 @@ combine_state_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp, const PixSta
     const int blk = (int)(item % Gm::NB);
     const uint32_t nch = cp.n_chunks[gt];
     if (nch <= 1) return;
+    // a list walked whole left every chunk's slot in the form pass 2 reads
+    const bool whole = whole_list(nch, whole_max(cp));
     const uint32_t s0 = cp.part_base[gt];
     if (s0 + nch > cp.slot_cap) return;
     const int vi = view_of_tile(*vsp, gt);
@@ -658,9 +720,9 @@ combine_state_kernel(const ViewSet *__restrict__ vsp, ChunkPlan cp, const PixSta
         const int py = bp.py0 + j;
         in[j] = bp.px < V.W && py < V.H;
         lp[j] = bp.lp0 + j * TW;
-        const int stop = in[j] ? ps[V.pix_base + (size_t)py * V.W + bp.px].stop : -1;
+        const int stop = (in[j] && !whole) ? ps[V.pix_base + (size_t)py * V.W + bp.px].stop : -1;
         top[j] = stop >= 0 ? (uint32_t)stop : nch - 1;
-        n_fwd[j] = !in[j] ? 0u : (stop < 0 ? top[j] + 1 : top[j]);
+        n_fwd[j] = (!in[j] || whole) ? 0u : (stop < 0 ? top[j] + 1 : top[j]);
     }
     {
         float t[PPT] = {1.f, 1.f}, h[PPT][5];
@@ -958,8 +1020,9 @@ __device__ __forceinline__ void block_scan2(uint32_t &a, uint32_t &b, uint32_t &
 }
 
 // In the last block: exclusive scan of the 256 bucket counts in aux, in
-// place (written by other blocks' atomics: read from L2).
-__device__ __forceinline__ void bucket_starts(uint32_t *aux) {
+// place (written by other blocks' atomics: read from L2); *total (if given)
+// receives their sum.
+__device__ __forceinline__ void bucket_starts(uint32_t *aux, uint32_t *total = nullptr) {
     __shared__ uint32_t sv[kOrderBuckets];
     for (uint32_t i = threadIdx.x; i < kOrderBuckets; i += blockDim.x) sv[i] = __ldcg(aux + i);
     __syncthreads();
@@ -982,6 +1045,7 @@ __device__ __forceinline__ void bucket_starts(uint32_t *aux) {
             aux[lane * per + j] = run;
             run += v;
         }
+        if (total && lane == 31) *total = inc;
     }
 }
 
@@ -999,9 +1063,10 @@ __device__ __forceinline__ bool last_block(uint32_t *ticket) {
 
 __global__ void __launch_bounds__(kPlanThreads)
 plan_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L, uint32_t *__restrict__ n_chunks,
-                  uint32_t *__restrict__ aux, uint32_t *__restrict__ counters) {
+                  uint32_t *__restrict__ aux, uint32_t *__restrict__ counters, ChunkPlan cp) {
     __shared__ uint32_t hist[kOrderBuckets];
     const int tid = threadIdx.x;
+    const uint32_t wmax = whole_max(cp);
     for (uint32_t i = tid; i < kOrderBuckets; i += kPlanThreads) hist[i] = 0;
     __syncthreads();
     const uint32_t t = blockIdx.x * kPlanThreads + tid;
@@ -1011,10 +1076,17 @@ plan_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L
         const uint32_t len = r.y - r.x;
         c = len > L + L / 2 ? (len + L - 1) / L : 1u; // up to 1.5 chunks stay one item
         n_chunks[t] = c;
-        // bucket k > 0 counts the tiles with more than k chunks
-        const uint32_t kc = min(c, kOrderBuckets - 1);
-        for (uint32_t k = 1; k < kc; ++k) atomicAdd(&hist[k], 1u);
-        if (c > kc) atomicAdd(&hist[kOrderBuckets - 1], c - kc);
+        // forward order: bucket 0 the lists one warp walks whole (the longest
+        // items, first), 1 the first chunks of the others, k + 1 the k-th later
+        // chunks of the lists walked chunk-parallel
+        if (whole_list(c, wmax)) {
+            atomicAdd(&hist[0], 1u);
+        } else {
+            atomicAdd(&hist[1], 1u);
+            const uint32_t kc = min(c, kOrderBuckets - 2);
+            for (uint32_t k = 1; k < kc; ++k) atomicAdd(&hist[k + 1], 1u);
+            if (c > kc) atomicAdd(&hist[kOrderBuckets - 1], c - kc);
+        }
     }
     uint32_t a = c, b = c > 1 ? c : 0u, ta, tb;
     block_scan2(a, b, ta, tb); // (synchronises: hist is complete)
@@ -1046,16 +1118,16 @@ plan_count_kernel(const uint2 *__restrict__ ranges, uint32_t n_tiles, uint32_t L
     if (tid == 0) {
         counters[4] = carry_a; // pairs
         counters[5] = carry_b; // slots
-        aux[0] = n_tiles;      // bucket 0: the first chunks
     }
     __syncthreads();
-    bucket_starts(aux);
+    bucket_starts(aux, counters + 7); // the forward's items (pairs in its order)
 }
 
 __global__ void __launch_bounds__(kPlanThreads)
 plan_place_kernel(uint32_t n_tiles, const uint32_t *__restrict__ n_chunks, uint32_t *__restrict__ chunk_base,
                   uint32_t *__restrict__ part_base, uint32_t *__restrict__ pair_tile, uint32_t pair_cap,
-                  uint32_t slot_cap, uint32_t *__restrict__ order, uint32_t *__restrict__ aux, uint32_t *status) {
+                  uint32_t slot_cap, uint32_t *__restrict__ order, uint32_t *__restrict__ aux, uint32_t *status,
+                  ChunkPlan cp) {
     const uint32_t t = blockIdx.x * kPlanThreads + threadIdx.x;
     const uint32_t c = t < n_tiles ? n_chunks[t] : 0u;
     uint32_t cb = c, pb = c > 1 ? c : 0u, ta, tb;
@@ -1072,19 +1144,33 @@ plan_place_kernel(uint32_t n_tiles, const uint32_t *__restrict__ n_chunks, uint3
             ok = false;
         }
     }
-    if (ok) {
+    if (ok)
         for (uint32_t k = 0; k < c; ++k) pair_tile[cb + k] = t;
-        order[t] = cb;
-    }
-    // later chunks: one atomic per warp and chunk index (the lanes that have
-    // a k-th chunk take consecutive positions)
-    const uint32_t kc = ok ? c : 0u;
-    const uint32_t kmax = __reduce_max_sync(0xffffffffu, kc);
+    // one atomic per warp and bucket (the lanes of one bucket take consecutive
+    // positions): first chunks by whether the list is walked whole, then the
+    // later chunks of the chunk-parallel lists by index
+    const bool whole = ok && whole_list(c, whole_max(cp));
     const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (uint32_t b = 0; b < 2; ++b) {
+        const bool mine = ok && (b == 0 ? whole : !whole);
+        const uint32_t m = __ballot_sync(0xffffffffu, mine);
+        if (!m) continue;
+        uint32_t base = 0;
+        if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(aux + b, (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+        if (mine) {
+            const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < pair_cap) order[pos] = cb;
+        }
+    }
+    const uint32_t kc = (ok && !whole) ? c : 0u;
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, kc);
     for (uint32_t k = 1; k < kmax; ++k) {
         const uint32_t m = __ballot_sync(0xffffffffu, k < kc);
         uint32_t base = 0;
-        if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(aux + min(k, kOrderBuckets - 1), (uint32_t)__popc(m));
+        if (lane == (uint32_t)(__ffs(m) - 1))
+            base = atomicAdd(aux + min(k + 1, kOrderBuckets - 1), (uint32_t)__popc(m));
         base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
         if (k < kc) {
             const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
@@ -1247,15 +1333,16 @@ void launch_plan(const ChunkPlan &cp, const uint2 *ranges, uint32_t n_tiles, uin
                  uint32_t *aux, uint32_t *status, cudaStream_t s) {
     if (n_tiles == 0) {
         cudaMemsetAsync(counters + 4, 0, 2 * sizeof(uint32_t), s);
+        cudaMemsetAsync(counters + 7, 0, sizeof(uint32_t), s);
         return;
     }
     const unsigned nb = (n_tiles + kPlanThreads - 1) / kPlanThreads;
     cudaMemsetAsync(aux, 0, sizeof(uint32_t) * kAuxBlocks, s);
     plan_count_kernel<<<nb, kPlanThreads, 0, s>>>(ranges, n_tiles, (uint32_t)cp.L, (uint32_t *)cp.n_chunks, aux,
-                                                  counters);
+                                                  counters, cp);
     plan_place_kernel<<<nb, kPlanThreads, 0, s>>>(n_tiles, cp.n_chunks, (uint32_t *)cp.chunk_base,
                                                   (uint32_t *)cp.part_base, (uint32_t *)cp.pair_tile, cp.pair_cap,
-                                                  cp.slot_cap, order, aux, status);
+                                                  cp.slot_cap, order, aux, status, cp);
 }
 
 void launch_bucket_place(const uint32_t *keys, const uint32_t *n_dev, uint32_t cap, uint32_t *aux, uint32_t *order,

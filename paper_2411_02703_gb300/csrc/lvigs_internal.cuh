@@ -214,6 +214,10 @@ struct ChunkPlan {
     const uint32_t *part_base;  // [tiles] first slot of a multi-chunk tile
     const uint32_t *pair_tile;  // [pair_cap] tile of each pair
     const uint32_t *n_pairs;    // device count of pairs
+    const uint32_t *n_fwd;      // device count of the forward's items (pairs in its order)
+    const uint32_t *n_inst;     // device count of the instances in the lists
+    int nb;                     // 8x8 blocks per tile
+    uint32_t warps;             // warps the compositing kernels keep resident
     float *part;                // [slot_cap] slots: 8 checkpoint groups of 6 x tile_w x tile_h floats
     uint32_t pair_cap, slot_cap;
     const uint32_t *pair_order; // [pair_cap] work order (chunk-major), or null
