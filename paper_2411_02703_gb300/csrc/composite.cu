@@ -345,7 +345,7 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
         const ViewDesc &V = vsp->v[vi];
         const BlockPix<TW, TH> bp(V, gt - V.tile_base, blk, lane);
         const uint2 rg = ranges[gt];
-        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT], Tin[PPT];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
         int last[PPT];
         bool done[PPT], stopped[PPT];
 #pragma unroll
@@ -370,10 +370,14 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
             Checkpoints ck{nullptr, cp.L / kSub, Gm::TPX, bp.lp0, TW};
             if (nch > 1 && !whole && cp.part_base[gt] + k < cp.slot_cap)
                 ck.g0 = slot_group(cp, cp.part_base[gt] + k, 0, 0, Gm::TPX);
+            // (a list walked whole parks the chunk's starting transmittance in
+            // the slot field it will fill, rather than in registers)
+            if (whole) {
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                Tin[j] = T[j];
-                if (whole) C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+                for (int j = 0; j < PPT; ++j) {
+                    slot_field(cp, cp.part_base[gt] + kk, 4, Gm::TPX)[bp.lp0 + j * TW] = T[j];
+                    C0[j] = C1[j] = C2[j] = D[j] = 0.f;
+                }
             }
             fwd_walk<BM, true, false>(inst_vals, recs, rg.x, lo, hi, (float)bp.px, bp.py0, bp.fx0, bp.fy0, sm, lane,
                                       T, C0, C1, C2, D, last, done, stopped, ck, nullptr);
@@ -389,7 +393,8 @@ composite_fwd_kernel(const ViewSet *__restrict__ vsp, const uint2 *__restrict__ 
                     slot_field(cp, slot, 1, Gm::TPX)[lp] = C1[j];
                     slot_field(cp, slot, 2, Gm::TPX)[lp] = C2[j];
                     slot_field(cp, slot, 3, Gm::TPX)[lp] = D[j];
-                    slot_field(cp, slot, 4, Gm::TPX)[lp] = Tin[j] - T[j];
+                    float *f4 = slot_field(cp, slot, 4, Gm::TPX) + lp;
+                    *f4 = *f4 - T[j];
                     slot_field(cp, slot, 5, Gm::TPX)[lp] = T[j];
                 }
             }
