@@ -18,7 +18,10 @@
 //            lies at or before that Gaussian).  Items run chunk-major (all
 //            first chunks, then all second chunks, ...) and a pixel whose local
 //            stop is published for an earlier chunk (a per-pixel atomicMin) is
-//            skipped by later chunks: they cannot contribute to it.
+//            skipped by later chunks: they cannot contribute to it.  A list of
+//            a few chunks (how many follows the work per warp) is instead one
+//            item, walked whole with the true transmittance: final here, its
+//            chunks' slots written in the backward's form, no phase 2.
 //   phase 2  per pixel the chunks are combined in order: C += T C_k,
 //            T *= T_k, until the chunk whose end would cross 1e-4 (2a); that
 //            chunk is walked again from the true T to find the exact stop, one
