@@ -89,7 +89,10 @@ def test_large_map_expansion_step():
     pgrads = {k: torch.zeros_like(dp[k]) for k in P.PARAM_NAMES}
     for i, c in enumerate(cams):
         rgb, depth, alpha, slot = ctx.render(dp, c, 0)
-        assert torch.equal(rgb, outs[i][0])
+        # bit-identical, or within float rounding where a list of a few chunks
+        # was walked whole in the batched step and chunk by chunk here
+        if not torch.equal(rgb, outs[i][0]):
+            assert float((rgb - outs[i][0]).abs().max()) <= 1e-5
         _, d_rgb, d_dep = ctx.loss(rgb, depth, gts[i], lis[i], 0.2, 0.1)
         ctx.backward(slot, dp, d_rgb, d_dep, grads=pgrads, accumulate=i > 0)
         ctx.release(slot)

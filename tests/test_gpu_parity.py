@@ -117,6 +117,25 @@ def assert_images(gpu, ref, alt, region=None, label=""):
     return cl
 
 
+# A list of a few chunks may be walked whole by one warp in a batched step
+# (the limit follows the work per warp) and chunk by chunk in a single-view
+# call; the two are then equal within float rounding, not bit for bit.
+SAME_RENDER_TOL = 1e-5
+
+
+def same_render(a, b, names=("rgb", "depth", "alpha")):
+    """True when the outputs are bit-identical; otherwise assert that they agree
+    within SAME_RENDER_TOL (depth relative to its largest value) and return False."""
+    if all(torch.equal(x, y) for x, y in zip(a, b)):
+        return True
+    for x, y, name in zip(a, b, names):
+        scale = max(1.0, float(y.abs().max())) if name == "depth" else 1.0
+        d = float((x - y).abs().max())
+        print(f"  {name}: {int((x != y).sum())} values differ, largest by {d:.2e}")
+        assert d <= SAME_RENDER_TOL * scale, name
+    return False
+
+
 def grad_check(name, g, r, r_alt=None, rtol=GRAD_RTOL):
     """Every element within rtol |r| + GRAD_FLOOR max|r|; with ``r_alt`` (the
     gradient of the flipped oracle step) widened by |r_alt - r|.
@@ -538,9 +557,9 @@ def test_batched_matches_plain_and_oracle(pkg):
         for _ in range(l):
             g_l, d_l = lv_p.pyramid_down(g_l, d_l)
         rgb, depth, alpha, slot = lv_p.render(dp, c, l)
-        assert torch.equal(rgb, outs[i][0]) and torch.equal(depth, outs[i][1]) and torch.equal(alpha, outs[i][2])
+        exact = same_render((rgb, depth, alpha), outs[i])
         terms, d_rgb, d_dep = lv_p.loss(rgb, depth, g_l, d_l, 0.2, 0.1)
-        np.testing.assert_allclose(terms.cpu().numpy(), losses[i].cpu().numpy(), rtol=1e-12)
+        np.testing.assert_allclose(terms.cpu().numpy(), losses[i].cpu().numpy(), rtol=1e-12 if exact else 1e-6)
         lv_p.backward(slot, dp, d_rgb, d_dep, grads=pgrads, accumulate=True)
         lv_p.release(slot)
     for k in pkg.PARAM_NAMES:
@@ -618,7 +637,7 @@ def test_autotune_then_batched_matches_plain(pkg):
     for i, (c, l) in enumerate(zip(cams, levels)):
         rgb, depth, alpha, slot = plain.render(dp, c, l)
         plain.release(slot)
-        assert torch.equal(rgb, outs[i][0]) and torch.equal(alpha, outs[i][2])
+        same_render((rgb, alpha), (outs[i][0], outs[i][2]), names=("rgb", "alpha"))
 
 
 @pytest.mark.parametrize("workload", ["lidar_200000_1v", "pyramid_500000", "lidar_1000000_8v"])
